@@ -1,0 +1,405 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the DEM timestep on GB300 (one JSON line on stdout).
+
+Workload (default `drum`): 4,194,304 spheres, radii U[0.9, 1.1] mm, dense bed in a drum
+of radius 300 mean radii and length 208 mean radii rotating at 2 rad/s about its
+horizontal axis, mu = 0.5, e = 0.7, practical model (Eqs. 2-10), linear stiffness
+k_n = 1e4 N/m, k_t = (2/7) k_n, dt = contact time of the smallest pair / 50, FP32
+forces with compensated positions, cell sort every step (Sec. 4.2). The bed is built by
+the seeded deposition generator and settled on the GPU for `--settle` steps before the
+warm-up; the working set (about 1.7 GB) is far larger than L2, so no flush is needed.
+
+One benchmark step is one timestep of the whole path: force pass (steps 5-8 and 1, with
+the new cell map of step 2) and cell sort (steps 3-4).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the FP64 C statement of the method, one core) on
+a bounded sample of the same workload. Under torchrun every rank runs an independent
+replica (replicas only: a single scene is not partitioned across GPUs); rank 0 prints.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-updates/s (practical model) & % HBM roofline vs simple model; served p50/p99"
+UNIT = "particle-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["drum", "rsa", "box"], default="drum")
+    ap.add_argument("--n", type=int, default=0, help="particle count (0 = the workload's own)")
+    ap.add_argument("--settle", type=int, default=2000)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--simple-steps", type=int, default=500)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ workload
+def make_scene(args, rank=0):
+    from paper_1301_1714_gb300 import scenes
+    seed = args.seed + 1000 * rank
+    if args.workload == "drum":
+        return scenes.drum(seed=seed, n=args.n or 4_194_304, precision="fp32")
+    if args.workload == "rsa":
+        return scenes.box_rsa(seed=seed, n=args.n or 262_144, precision="fp32")
+    return scenes.box_lattice(seed=seed, precision="fp64")
+
+
+def workload_desc(args, sc):
+    p = sc.params
+    if args.workload == "drum":
+        return (f"drum: {sc.n:,} spheres r~U[0.9,1.1] mm, drum R=300r L=208r rotating 2 rad/s, mu={p.mu}, e=0.7, "
+                f"practical linear kn={p.kn:g} N/m, dt={p.dt:.5e} s, FP32 forces + compensated positions, sort every step")
+    if args.workload == "rsa":
+        return f"box settling: {sc.n:,} spheres r~U[0.8,1.2] mm, RSA loose fill, practical linear, FP32"
+    return f"box: {sc.n:,} spheres r=1 mm, jittered lattice, practical linear, FP64"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [t.strip() for t in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[4 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def physical_gpu_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return local_rank
+
+
+# ------------------------------------------------------------------ roofline inputs
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for fn in ("dem_kernels.cu", "dem_dev.cuh"):
+        with open(os.path.join(ROOT, "paper_1301_1714_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic_per_particle():
+    """DRAM bytes per particle of the force kernel from the committed ncu summary, if it
+    was taken on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "force_kernel_drum.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    src, bpp = None, None
+    for line in txt.splitlines():
+        if line.startswith("kernel_source_sha256_16:"):
+            src = line.split(":", 1)[1].strip()
+        if line.startswith("dram_bytes_per_particle:"):
+            try:
+                bpp = float(line.split(":", 1)[1].strip())
+            except ValueError:
+                bpp = None
+    return bpp if (src == kernel_source_hash() and bpp) else None
+
+
+# ------------------------------------------------------------------ oracle sample
+def oracle_sample(args, sc, target_s, max_steps=None):
+    """Time the FP64 oracle on a slab of the workload (particles with x below a cut),
+    sized so that the steps take about target_s seconds. Returns (value, sample text,
+    steps, seconds)."""
+    import oracle
+    order = np.argsort(sc.x[:, 0], kind="stable")
+    # calibrate on a small slab
+    n_cal = min(sc.n, 20000)
+    sel = np.sort(order[:n_cal])
+    t0 = time.perf_counter()
+    oracle.State(sc.params.copy(precision="fp64"), sc.x[sel], sc.v[sel], sc.w[sel], sc.r[sel]).run(1)
+    per = (time.perf_counter() - t0) / n_cal
+    steps = max(1, min(max_steps or 3, 3))
+    n_s = int(min(sc.n, max(1000, target_s / (per * steps))))
+    sel = np.sort(order[:n_s])
+    st = oracle.State(sc.params.copy(precision="fp64"), sc.x[sel], sc.v[sel], sc.w[sel], sc.r[sel])
+    t0 = time.perf_counter()
+    st.run(steps)
+    dt = time.perf_counter() - t0
+    value = n_s * steps / dt
+    xcut = float(sc.x[sel, 0].max())
+    desc = (f"FP64 oracle (C, 1 thread), {steps} step(s) of the {n_s:,} spheres with x <= {xcut:.4f} m of the same "
+            f"seeded workload before settling (grid pair search), {dt:.1f} s")
+    return value, desc, steps, dt
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import torch
+    from paper_1301_1714_gb300 import dem
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local_rank if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(device=dev)
+
+    sc = make_scene(args, rank)
+    p = sc.params
+    N = sc.n
+    cfg = dem.config_from_params(p)
+    h = dem.dem_create(cfg, dev.index, stream.cuda_stream)
+    try:
+        dem.dem_set_walls(h, p.walls)
+        dem.dem_set_particles(h, sc.x, sc.v, sc.w, sc.r)
+        if args.settle:
+            dem.dem_step(h, args.settle)
+        dem.dem_step(h, max(3, args.warmup))
+        # ---------------- timed region (device events on the library's stream)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        dem.dem_set_timing(h, True)
+        l0 = dem.dem_launch_count(h)
+        clk = ClockSampler(physical_gpu_index(local_rank))
+        clk.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        dem.dem_step(h, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        clocks = clk.stop()
+        if dist:
+            dist.barrier()
+        launches = dem.dem_launch_count(h) - l0
+        ms = e0.elapsed_time(e1)
+        phase = dem.dem_get_phase_times(h)
+        dem.dem_set_timing(h, False)
+        diag = dict(zip(dem.DIAG_NAMES, dem.dem_get_diagnostics(h)))
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            tot = torch.tensor([float(N)], device=dev, dtype=torch.float64)
+            dist.all_reduce(tot)
+            n_total = float(tot.item())
+        else:
+            n_total = float(N)
+        value = n_total * args.steps / (ms / 1e3)
+
+        # ---------------- roofline of the dominant kernel (force pass)
+        Z = 2.0 * diag["pair_contacts"] / N
+        W = diag["wall_contacts"] / N
+        b_force = 104.0 + 20.0 * Z + 40.0 * W
+        force_ms = phase[0] / max(phase[2], 1)
+        sort_ms = phase[1] / max(phase[3], 1)
+        peak, peak_src = measured_hbm_gbs()
+        achieved = b_force * N / (force_ms / 1e3) / 1e9
+        bpp = profiled_traffic_per_particle()
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": (round(bpp * N) if bpp else None),
+                "kernel": "k_force<PF32,practical>", "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "algorithmic_bytes_per_particle": round(b_force, 1), "Z": round(Z, 3), "W": round(W, 4),
+                "force_ms": round(force_ms, 4), "sort_ms": round(sort_ms, 4)}
+
+        # ---------------- practical / simple on the same settled bed
+        xs, vs, ws = dem.dem_get_state(h, N)
+        simple = None
+        if args.simple_steps > 0:
+            hs = dem.dem_create(dem.config_from_params(p.copy(model="simple")), dev.index, stream.cuda_stream)
+            try:
+                dem.dem_set_walls(hs, p.walls)
+                dem.dem_set_particles(hs, xs, vs, ws, sc.r)
+                dem.dem_step(hs, 3)
+                torch.cuda.synchronize(dev)
+                dem.dem_set_timing(hs, True)
+                s0 = torch.cuda.Event(enable_timing=True)
+                s1 = torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+                dem.dem_step(hs, args.simple_steps)
+                s1.record(stream)
+                torch.cuda.synchronize(dev)
+                sms = s0.elapsed_time(s1)
+                sph = dem.dem_get_phase_times(hs)
+                simple = {"value": round(N * args.simple_steps / (sms / 1e3), 1),
+                          "ms_per_step": round(sms / args.simple_steps, 4),
+                          "force_ms": round(sph[0] / max(sph[2], 1), 4),
+                          "practical_over_simple_slowdown": round((ms / args.steps) / (sms / args.simple_steps), 3)}
+            finally:
+                dem.dem_destroy(hs)
+
+        # ---------------- end to end through the C ABI with host buffers
+        e2e = None
+        if not args.no_e2e:
+            pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+            hx, hv, hw, hr = pin(xs), pin(vs), pin(ws), pin(sc.r)
+            ox = torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy()
+            ov = torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy()
+            ow = torch.empty((N, 3), dtype=torch.float64).pin_memory().numpy()
+            he = dem.dem_create(cfg, dev.index, stream.cuda_stream)
+            try:
+                dem.dem_set_walls(he, p.walls)
+                dem.dem_set_particles(he, hx, hv, hw, hr)      # allocate once outside the timed region
+                torch.cuda.synchronize(dev)
+                if dist:
+                    dist.barrier()
+                t0 = time.perf_counter()
+                dem.dem_set_particles(he, hx, hv, hw, hr)
+                dem.dem_step(he, args.steps)
+                r_ = dem.lib().dem_get_state(he, dem._ptr(ox), dem._ptr(ov), dem._ptr(ow), dem.DEM_HOST)
+                if r_ != 0:
+                    raise dem.DemError(r_, dem.dem_last_error(he))
+                te = time.perf_counter() - t0
+                if dist:
+                    t = torch.tensor([te], device=dev)
+                    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                    te = float(t.item())
+            finally:
+                dem.dem_destroy(he)
+            h2d = N * (3 * 24 + 4)
+            d2h = N * 3 * 24
+            e2e = {"value": round(n_total * args.steps / te, 1), "unit": UNIT,
+                   "h2d_bytes_per_step": round(h2d / args.steps, 1), "d2h_bytes_per_step": round(d2h / args.steps, 1),
+                   "note": "one upload of the state, K steps, one download of the state (pinned host buffers), "
+                           "through dem_set_particles / dem_step / dem_get_state"}
+
+        out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+               "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": workload_desc(args, sc), "n_particles": N, "seed": args.seed,
+                          "settle_steps": args.settle, "resort_interval": 1,
+                          "l2": "inputs larger than L2 (no flush needed)",
+                          "device_bytes": dem.dem_device_bytes(h), "parallelism": f"replicas x{world}"},
+               "roofline": roof, "gpu_launches": int(launches), "clocks": clocks, "simple": simple, "e2e": e2e,
+               "diagnostics": {k: diag[k] for k in ("pair_contacts", "wall_contacts", "max_overlap", "ke_trans")}}
+    finally:
+        dem.dem_destroy(h)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, desc, steps, dt = oracle_sample(args, sc, args.cpu_seconds)
+        out["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    elif rank == 0:
+        out["cpu_baseline"] = None
+    if dist:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    sc = make_scene(args, 0)
+    steps = args.steps + max(3, args.warmup)
+    # the whole run (warm-up + timed steps) should take a few minutes: size the sample
+    import oracle
+    order = np.argsort(sc.x[:, 0], kind="stable")
+    n_cal = min(sc.n, 20000)
+    sel = np.sort(order[:n_cal])
+    t0 = time.perf_counter()
+    oracle.State(sc.params.copy(precision="fp64"), sc.x[sel], sc.v[sel], sc.w[sel], sc.r[sel]).run(1)
+    per = (time.perf_counter() - t0) / n_cal
+    budget = 150.0
+    n_s = int(min(sc.n, max(500, budget / (per * steps))))
+    sel = np.sort(order[:n_s])
+    st = oracle.State(sc.params.copy(precision="fp64"), sc.x[sel], sc.v[sel], sc.w[sel], sc.r[sel])
+    st.run(max(3, args.warmup))
+    t0 = time.perf_counter()
+    st.run(args.steps)
+    dt = time.perf_counter() - t0
+    value = n_s * args.steps / dt
+    desc = (f"FP64 oracle (C, 1 thread) on the {n_s:,} spheres with x <= {float(sc.x[sel, 0].max()):.4f} m of the "
+            f"same seeded workload, {args.steps} timed steps after {max(3, args.warmup)} warm-up steps")
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(dt * 1e3 / args.steps, 3),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": workload_desc(args, sc), "n_particles": sc.n, "seed": args.seed},
+           "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
+           "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * dem.h -- C ABI of the GB300 soft-sphere DEM timestep library (libdemgb.so).
+ *
+ * The library advances spherical particles by the method of Washizawa & Nakahara,
+ * "Parallel Computing of Discrete Element Method on GPU": each timestep
+ *   1. updates all particle properties (Sec. 4.2 step 1; semi-implicit Euler here),
+ *   2. maps every particle to a cell of a uniform grid, CM (Sec. 4.1; step 2),
+ *   3. sorts particles by cell, giving SCM and the permutation SCCM (Eq. 11; step 3),
+ *   4. reorders every particle property into that order (step 4),
+ *   5-7. evaluates the contact force of each particle against the 27 surrounding cells
+ *      (Eq. 12) with the simple model (Eq. 1) or the practical model (Eqs. 2-10),
+ *   8. adds particle-wall contacts (a wall is a particle of infinite radius).
+ *
+ * Conventions for every function:
+ *  - Return a dem_status; never abort the process. On failure a message is available
+ *    from dem_last_error(h). A failed call leaves the handle usable unless the status is
+ *    DEM_ERR_CUDA (a CUDA error), after which only dem_destroy is valid.
+ *  - Arrays passed in or out are owned by the caller. Inputs are copied; the library
+ *    keeps no pointer after the call returns.
+ *  - `where` says whether a pointer is host memory (DEM_HOST) or device memory on the
+ *    handle's device (DEM_DEVICE). Device pointers are read or written in order on the
+ *    handle's CUDA stream.
+ *  - Per-particle arrays are in GLOBAL-ID order: element k belongs to particle id k.
+ *    Vectors are interleaved (x0 y0 z0 x1 y1 z1 ...), SI units, double precision.
+ *  - Functions that return data synchronise the handle's stream before returning.
+ *    dem_step enqueues its work and synchronises once at its end to read the status word.
+ *  - The library is not thread-safe per handle; distinct handles may be used from
+ *    distinct threads.
+ */
+#ifndef DEM_GB300_H
+#define DEM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DEM_OK = 0,
+    DEM_ERR_INVALID_ARG = 1,  /* a pointer, size or parameter is out of range */
+    DEM_ERR_OOM = 2,          /* a device or host allocation failed */
+    DEM_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    DEM_ERR_CAPACITY = 4,     /* a particle had more contacts than max_contacts */
+    DEM_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
+    DEM_ERR_NONFINITE = 6,    /* a position or velocity became NaN/Inf */
+    DEM_ERR_STATE = 7         /* call order: e.g. dem_step before dem_set_particles */
+} dem_status;
+
+enum { DEM_PRACTICAL = 0, DEM_SIMPLE = 1 };   /* contact model: Eqs. 2-10 or Eq. 1 */
+enum { DEM_LINEAR = 0, DEM_HERTZ = 1 };       /* stiffness: constant k, or Eqs. 8-9 */
+enum { DEM_FP64 = 0, DEM_FP32 = 1 };          /* precision mode, see dem_config */
+enum { DEM_HOST = 0, DEM_DEVICE = 1 };
+enum { DEM_PLANE = 0, DEM_CYLINDER_IN = 1 };
+
+/* Parameters of one scene (Sec. 3 "particle properties" and the grid of Sec. 4.1).
+ *  model       DEM_PRACTICAL: F = F_t + F_n (Eq. 2), torque r_i n x F_t (Eq. 3),
+ *              spring-dashpots (Eq. 4) with Coulomb cap (Eq. 5), slip velocity (Eq. 6),
+ *              tangential spring history (Eq. 7), stiffness (Eqs. 8-9), damping (Eq. 10).
+ *              DEM_SIMPLE: F = -k_sp delta n - k_da v - k_sh v_t (Eq. 1), no torque.
+ *  stiffness   DEM_LINEAR: k_n = kn, k_t = kt. DEM_HERTZ: k = C sqrt(delta R_eff) with
+ *              C = cn (normal) or ct (tangential), Eqs. 8-9.
+ *  precision   DEM_FP64: every quantity and operation in FP64; contact and cell
+ *              decisions are the FP64 ones of the reference formulas.
+ *              DEM_FP32: velocities, spins, forces, torques and tangential springs in
+ *              FP32; positions as an unevaluated sum of two FP32 numbers (compensated,
+ *              about 48 significant bits); the overlap delta and the contact decision
+ *              are computed with error-free transformations; cells are hashed in FP32.
+ *  dt          timestep [s]; rho density [kg/m^3] (m = rho 4/3 pi r^3, I = 2/5 m r^2)
+ *  g           gravitational acceleration [m/s^2], added as m g once per particle
+ *  kn, kt      linear stiffnesses [N/m]; cn, ct Hertz coefficients [N/m^1.5... see Eqs. 8-9]
+ *  alpha       restitution parameter of Eq. 10: eta = alpha sqrt(k_n m_eff)
+ *  mu          kinetic friction coefficient of Eq. 5
+ *  ksp,kda,ksh spring, damping and shear coefficients of Eq. 1
+ *  skin        Verlet skin [m]: with resort_interval != 1 the cell size grows by skin
+ *              and the cell sort is skipped while every particle moved less than skin/2
+ *  cell_size   grid cell edge [m]; 0 = 2 r_max (1 + 2^-10) + skin, r_max the largest
+ *              radius passed to dem_set_particles. Must be >= that value.
+ *  domain_lo/hi  box covered by the grid; particles outside use the nearest face cell.
+ *  resort_interval 1 = sort every step (as in Sec. 4.2); 0 = automatic (skin-driven)
+ *  block_size  threads per block of the force kernel; 0 = automatic (128)
+ *  max_contacts  per-particle capacity of the contact/history list (incl. walls);
+ *              0 = 32. Exceeding it makes dem_step return DEM_ERR_CAPACITY.
+ */
+typedef struct {
+    int32_t model;
+    int32_t stiffness;
+    int32_t precision;
+    int32_t resort_interval;
+    double dt, rho, g[3];
+    double kn, kt, cn, ct, alpha, mu;
+    double ksp, kda, ksh;
+    double skin, cell_size;
+    double domain_lo[3], domain_hi[3];
+    int32_t block_size;
+    int32_t max_contacts;
+} dem_config;
+
+/* A wall (Sec. 4.2 step 8): a body of infinite radius and mass.
+ *  DEM_PLANE        plane through p with unit normal n pointing INTO the domain;
+ *                   a sphere touches it when its centre is closer than r.
+ *  DEM_CYLINDER_IN  inside of a cylinder of the given radius whose axis passes through
+ *                   p along the unit vector n (in DEM_FP32 mode n must be a coordinate
+ *                   axis); a sphere touches it when its centre is farther than
+ *                   radius - r from the axis.
+ *  omega, vel       the wall surface moves with velocity vel + omega x (c - p) at a
+ *                   point c; this velocity replaces the partner's in Eq. 6.
+ */
+typedef struct {
+    int32_t kind;
+    int32_t pad;
+    double p[3], n[3];
+    double radius;
+    double omega[3], vel[3];
+} dem_wall;
+
+typedef struct dem_handle dem_handle;
+
+/* Creates a handle on CUDA device `device` whose work runs on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream). Validates cfg. */
+dem_status dem_create(const dem_config* cfg, int device, void* cuda_stream, dem_handle** out);
+
+/* Sets n particles (Sec. 3 particle properties): positions x, velocities v, spins w
+ * (3n doubles each, id order) and radii r (n floats, > 0). id must be NULL: particle k
+ * has global id k. Clears the tangential history. Allocates device memory as needed
+ * and performs the first cell sort (steps 2-4). n may be 0. */
+dem_status dem_set_particles(dem_handle* h, int64_t n, const uint32_t* id, const double* x, const double* v,
+                             const double* w, const float* r, int where);
+
+/* Replaces the walls (at most 8). Keeps particle state; clears wall histories. */
+dem_status dem_set_walls(dem_handle* h, int nwalls, const dem_wall* walls);
+
+/* Advances nsteps timesteps (each: forces of steps 5-8 at the current state, update of
+ * step 1, then steps 2-4 for the new positions). Returns the first error raised on the
+ * device during these steps (DEM_ERR_CAPACITY, DEM_ERR_NONFINITE), after which the state
+ * is the one reached when the error was detected at the end of the call. */
+dem_status dem_step(dem_handle* h, int64_t nsteps);
+
+/* Copies the current state out in id order (any pointer may be NULL to skip it). */
+dem_status dem_get_state(dem_handle* h, double* x, double* v, double* w, int where);
+
+/* Evaluates the force and torque on every particle at the current state (steps 5-8 and
+ * gravity) without advancing time; 3n doubles each in id order (NULL skips). The
+ * contact pairs found are kept for dem_debug_snapshot. */
+dem_status dem_get_forces(dem_handle* h, double* F, double* T, int where);
+
+/* Tangential springs currently stored, one record per contact: particle pairs as
+ * (i, j) with i < j and the spring seen from i (n from i to j, v = v_i - v_j); wall
+ * contacts as (i, 0xFFFFFF00 + wall index). Records are sorted by (i, j). Host memory.
+ * *n receives the number of records; at most cap are written. */
+dem_status dem_get_history(dem_handle* h, int64_t cap, uint32_t* i, uint32_t* j, double* d, int64_t* n);
+
+/* Restores a state and its tangential springs (records as returned by dem_get_history,
+ * host memory). Equivalent to dem_set_particles followed by setting the springs; a
+ * restored run continues exactly as the saved one would have. */
+dem_status dem_restore(dem_handle* h, int64_t n, const double* x, const double* v, const double* w, const float* r,
+                       int64_t nrec, const uint32_t* i, const uint32_t* j, const double* d);
+
+/* Diagnostics of the current state, reduced in FP64 in a fixed order (host array of 16):
+ * [0] translational KE, [1] rotational KE, [2..4] linear momentum, [5..7] angular
+ * momentum about the origin (m x cross v + I w), [8] gravitational potential energy
+ * (-m g.x), [9] total mass, [10] number of particle-particle contacts, [11] number of
+ * particle-wall contacts, [12] largest overlap (of the last force evaluation),
+ * [13] steps taken since dem_set_particles, [14] cell sorts performed,
+ * [15] particles whose cell index was clamped to the grid. */
+dem_status dem_get_diagnostics(dem_handle* h, double* out16);
+
+/* Parity hooks (host memory). cell: cell key of each particle (id order) as of the last
+ * sort; order: particle ids in (cell, id) order (SCCM of Eq. 11); pairs: the contact
+ * pairs (i < j, sorted) of the last dem_get_forces call, 2 per pair, at most pair_cap
+ * pairs written; *npairs receives the count. Any output pointer may be NULL. */
+dem_status dem_debug_snapshot(dem_handle* h, uint32_t* cell, uint32_t* order, int64_t pair_cap, uint32_t* pairs,
+                              int64_t* npairs);
+
+/* The grid in use: origin (3), cell edge, and cells per axis (3). */
+dem_status dem_get_grid(const dem_handle* h, double* origin, double* cell, int64_t* dims);
+
+/* Phase timing. While enabled, dem_step records a CUDA event pair around every force
+ * pass (steps 5-8, 1 and the new cell map of step 2) and every cell sort (steps 3-4) on
+ * the handle's stream; the device times are accumulated when dem_step synchronises.
+ * dem_set_timing(h, 1) also clears the totals. out4: [0] force-pass milliseconds,
+ * [1] sort milliseconds, [2] force passes timed, [3] sorts timed. */
+dem_status dem_set_timing(dem_handle* h, int enable);
+dem_status dem_get_phase_times(const dem_handle* h, double* out4);
+
+/* Bytes of device memory held by the handle. */
+int64_t dem_device_bytes(const dem_handle* h);
+
+/* Number of kernel launches the handle has enqueued so far. */
+int64_t dem_launch_count(const dem_handle* h);
+
+/* Last error message of the handle ("" if none). Valid until the next call on h. */
+const char* dem_last_error(const dem_handle* h);
+
+/* Frees the handle and its device memory. NULL is allowed. */
+void dem_destroy(dem_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DEM_GB300_H */

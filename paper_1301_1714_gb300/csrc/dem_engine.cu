@@ -1,0 +1,796 @@
+// Host engine behind the C ABI of include/dem.h: validation, device buffers, the
+// per-step launch sequence and the read-out paths.
+//
+// One dem_step = force pass (steps 5-8 and step 1, which also computes the new cell map
+// CM of step 2 and each particle's rank within its cell) followed by the cell sort
+// (steps 3-4: scan of the cell counts, scatter, (cell, id) order and gather).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dem.h"
+#include "dem_domain.h"
+
+using namespace demgb;
+
+struct dem_handle {
+    Domain d;
+    dem_config cfg{};
+    int device = 0;
+    std::vector<dem_wall> walls;
+    double rmax = 0.0;
+    double origin[3] = {0, 0, 0};
+    double h = 0.0;
+    int64_t dims[3] = {1, 1, 1};
+    bool has_particles = false;
+    bool broken = false;
+    bool eval_valid = false;
+    int64_t steps = 0;
+    std::string err;
+    // phase timing (events around force passes and sorts)
+    bool timing = false;
+    std::vector<cudaEvent_t> events;
+    double t_force_ms = 0.0, t_sort_ms = 0.0;
+    int64_t n_force = 0, n_sort = 0;
+    // staging for host <-> device transfers (x, v, w: 3n doubles each; r: n floats)
+    double* stage = nullptr;
+    float* stage_r = nullptr;
+    uint32_t stage_cap = 0;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+dem_status fail(dem_handle* h, dem_status s, const std::string& msg) {
+    if (h) h->err = msg;
+    return s;
+}
+
+dem_status cuda_fail(dem_handle* h, cudaError_t e, const char* what) {
+    if (h) {
+        h->broken = true;
+        h->err = std::string(what) + ": " + cudaGetErrorString(e);
+    }
+    return DEM_ERR_CUDA;
+}
+
+#define CK(h, expr)                                                        \
+    do {                                                                   \
+        cudaError_t e__ = (expr);                                          \
+        if (e__ != cudaSuccess) return cuda_fail((h), e__, #expr);         \
+    } while (0)
+
+template <class P>
+cudaError_t dmalloc(Domain& d, P** p, size_t bytes) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, bytes ? bytes : 16);
+    if (e != cudaSuccess) return e;
+    d.allocations.push_back(q);
+    *p = (P*)q;
+    return cudaSuccess;
+}
+
+void free_particle_buffers(Domain& d) {
+    for (void* p : d.allocations) cudaFree(p);
+    d.allocations.clear();
+    d.A64 = StateF64{};
+    d.B64 = StateF64{};
+    d.A32 = StateF32{};
+    d.B32 = StateF32{};
+    for (int i = 0; i < 2; ++i) { d.hcnt[i] = nullptr; d.hpid[i] = nullptr; d.hd[i] = nullptr; }
+    d.key = d.rank = d.tmp = d.perm = d.skey = d.cnt = d.cs = d.part = nullptr;
+    d.diag_part = nullptr;
+    d.cap = 0;
+    d.cells_cap = 0;
+    d.part_cap = 0;
+    d.diag_part_cap = 0;
+}
+
+bool finite3(const double* a) { return std::isfinite(a[0]) && std::isfinite(a[1]) && std::isfinite(a[2]); }
+
+void split_f(double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+// Fill a WallDev from a dem_wall.
+WallDev make_wall(const dem_wall& w) {
+    WallDev W{};
+    W.kind = w.kind;
+    W.axis = -1;
+    for (int a = 0; a < 3; ++a) {
+        W.p[a] = w.p[a];
+        W.n[a] = w.n[a];
+        W.omega[a] = w.omega[a];
+        W.vel[a] = w.vel[a];
+        split_f(w.p[a], W.p_hi[a], W.p_lo[a]);
+        split_f(w.n[a], W.n_hi[a], W.n_lo[a]);
+        W.nf[a] = (float)w.n[a];
+        W.omegaf[a] = (float)w.omega[a];
+        W.velf[a] = (float)w.vel[a];
+        W.pf[a] = (float)w.p[a];
+    }
+    W.radius = w.radius;
+    split_f(w.radius, W.rad_hi, W.rad_lo);
+    // coordinate-axis normal / axis
+    for (int a = 0; a < 3; ++a) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        if (std::fabs(w.n[a]) == 1.0 && w.n[b] == 0.0 && w.n[c] == 0.0) W.axis = a;
+    }
+    return W;
+}
+
+void fill_scene(dem_handle* h, SceneDev& S, uint32_t p0, uint32_t np, uint32_t c0) {
+    const dem_config& c = h->cfg;
+    S = SceneDev{};
+    S.p0 = p0;
+    S.np = np;
+    S.c0 = c0;
+    S.ncell = (uint32_t)(h->dims[0] * h->dims[1] * h->dims[2]);
+    for (int a = 0; a < 3; ++a) {
+        S.dims[a] = (int32_t)h->dims[a];
+        S.origin[a] = h->origin[a];
+        S.origin_f[a] = (float)h->origin[a];
+        S.g[a] = c.g[a];
+        S.g_f[a] = (float)c.g[a];
+    }
+    S.h = h->h;
+    S.h_f = (float)h->h;
+    S.active = 1;
+    S.nwalls = (int32_t)h->walls.size();
+    S.dt = c.dt; S.kn = c.kn; S.kt = c.kt; S.cn = c.cn; S.ct = c.ct; S.alpha = c.alpha; S.mu = c.mu;
+    S.ksp = c.ksp; S.kda = c.kda; S.ksh = c.ksh;
+    S.cmass = c.rho * (4.0 / 3.0) * 3.14159265358979323846;
+    S.dt_f = (float)c.dt; S.kn_f = (float)c.kn; S.kt_f = (float)c.kt; S.cn_f = (float)c.cn; S.ct_f = (float)c.ct;
+    S.alpha_f = (float)c.alpha; S.mu_f = (float)c.mu; S.ksp_f = (float)c.ksp; S.kda_f = (float)c.kda;
+    S.ksh_f = (float)c.ksh; S.cmass_f = (float)S.cmass;
+    // FP32 prefilter margin: bounds the FP32 error of |hi_j - hi_i| for coordinates up to X
+    double X = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double ext = c.domain_hi[a] - c.domain_lo[a];
+        X = std::max(X, std::max(std::fabs(c.domain_lo[a]), std::fabs(c.domain_hi[a])) + ext);
+    }
+    S.eps_f = (float)(std::ldexp(1.0, -20) * (X + 2.0 * h->rmax));
+    for (size_t k = 0; k < h->walls.size(); ++k) S.walls[k] = make_wall(h->walls[k]);
+}
+
+dem_status validate_config(const dem_config* c, std::string& why) {
+    if (!c) { why = "cfg is NULL"; return DEM_ERR_INVALID_ARG; }
+    if (c->model != DEM_PRACTICAL && c->model != DEM_SIMPLE) { why = "model"; return DEM_ERR_INVALID_ARG; }
+    if (c->stiffness != DEM_LINEAR && c->stiffness != DEM_HERTZ) { why = "stiffness"; return DEM_ERR_INVALID_ARG; }
+    if (c->precision != DEM_FP64 && c->precision != DEM_FP32) { why = "precision"; return DEM_ERR_INVALID_ARG; }
+    if (!(c->dt > 0.0) || !std::isfinite(c->dt)) { why = "dt must be > 0"; return DEM_ERR_INVALID_ARG; }
+    if (!(c->rho > 0.0) || !std::isfinite(c->rho)) { why = "rho must be > 0"; return DEM_ERR_INVALID_ARG; }
+    if (!finite3(c->g)) { why = "g"; return DEM_ERR_INVALID_ARG; }
+    const double nonneg[] = {c->kn, c->kt, c->cn, c->ct, c->alpha, c->mu, c->ksp, c->kda, c->ksh, c->skin, c->cell_size};
+    for (double v : nonneg)
+        if (!(v >= 0.0) || !std::isfinite(v)) { why = "stiffness, damping, friction, skin and cell_size must be finite and >= 0"; return DEM_ERR_INVALID_ARG; }
+    for (int a = 0; a < 3; ++a)
+        if (!(c->domain_hi[a] > c->domain_lo[a]) || !std::isfinite(c->domain_lo[a]) || !std::isfinite(c->domain_hi[a])) {
+            why = "domain_hi must exceed domain_lo on every axis";
+            return DEM_ERR_INVALID_ARG;
+        }
+    if (c->resort_interval < 0) { why = "resort_interval"; return DEM_ERR_INVALID_ARG; }
+    if (c->block_size != 0 && (c->block_size < 32 || c->block_size > 256 || c->block_size % 32)) {
+        why = "block_size must be 0 or a multiple of 32 in [32, 256]";
+        return DEM_ERR_INVALID_ARG;
+    }
+    if (c->max_contacts < 0 || c->max_contacts > 64) { why = "max_contacts must be in [0, 64]"; return DEM_ERR_INVALID_ARG; }
+    return DEM_OK;
+}
+
+// (Re)allocate particle and cell buffers for n particles and ncells cells.
+dem_status ensure_buffers(dem_handle* h, uint32_t n, uint32_t ncells) {
+    Domain& d = h->d;
+    const uint32_t need = std::max<uint32_t>(n, 1);
+    if (need <= d.cap && ncells <= d.cells_cap) return DEM_OK;
+    free_particle_buffers(d);
+    const uint32_t cap = std::max<uint32_t>(need, 64);
+    const uint32_t ccap = std::max<uint32_t>(ncells, 1);
+    const size_t N = cap;
+    const size_t T = d.precision == 0 ? sizeof(double) : sizeof(float);
+    cudaError_t e = cudaSuccess;
+#define AL(ptr, bytes) do { if ((e = dmalloc(d, &(ptr), (bytes))) != cudaSuccess) { free_particle_buffers(d); return fail(h, DEM_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e)); } } while (0)
+    for (int s = 0; s < 2; ++s) {
+        if (d.precision == 0) {
+            StateF64& S = s == 0 ? d.A64 : d.B64;
+            AL(S.x, N * 8); AL(S.y, N * 8); AL(S.z, N * 8);
+            AL(S.vx, N * 8); AL(S.vy, N * 8); AL(S.vz, N * 8);
+            AL(S.wx, N * 8); AL(S.wy, N * 8); AL(S.wz, N * 8);
+            AL(S.r, N * 4); AL(S.id, N * 4);
+        } else {
+            StateF32& S = s == 0 ? d.A32 : d.B32;
+            AL(S.P0, N * 16); AL(S.P1, N * 16); AL(S.V, N * 16); AL(S.W, N * 16); AL(S.id, N * 4);
+        }
+        AL(d.hcnt[s], N * 4);
+        AL(d.hpid[s], N * 4 * (size_t)d.maxc);
+        AL(d.hd[s], N * T * 3 * (size_t)d.maxc);
+    }
+    AL(d.key, N * 4); AL(d.rank, N * 4); AL(d.tmp, N * 4); AL(d.perm, N * 4); AL(d.skey, N * 4);
+    AL(d.cnt, ((size_t)ccap + 1) * 4);
+    AL(d.cs, ((size_t)ccap + 1) * 4);
+    const uint32_t nb = (ccap + 1 + 2047) / 2048;
+    AL(d.part, (size_t)nb * 4);
+    const uint32_t db = (cap + 255) / 256;
+    AL(d.diag_part, (size_t)db * 10 * 8);
+#undef AL
+    d.cap = cap;
+    d.cells_cap = ccap;
+    d.part_cap = nb;
+    d.diag_part_cap = db;
+    e = cudaMemsetAsync(d.cnt, 0, ((size_t)ccap + 1) * 4, d.stream);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync(cnt)");
+    return DEM_OK;
+}
+
+dem_status ensure_stage(dem_handle* h, uint32_t n) {
+    if (n <= h->stage_cap && h->stage) return DEM_OK;
+    if (h->stage) cudaFree(h->stage);
+    if (h->stage_r) cudaFree(h->stage_r);
+    h->stage = nullptr;
+    h->stage_r = nullptr;
+    h->stage_cap = 0;
+    const uint32_t cap = std::max<uint32_t>(n, 64);
+    if (cudaMalloc(&h->stage, (size_t)cap * 9 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->stage_r, (size_t)cap * sizeof(float)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, DEM_ERR_OOM, "cudaMalloc of the staging buffer failed");
+    }
+    h->stage_cap = cap;
+    return DEM_OK;
+}
+
+dem_status sync_status(dem_handle* h) {
+    Domain& d = h->d;
+    CK(h, cudaMemcpyAsync(d.st_host, d.st, sizeof(StatusDev), cudaMemcpyDeviceToHost, d.stream));
+    CK(h, cudaStreamSynchronize(d.stream));
+    if (d.st_host->code != 0) {
+        const int code = d.st_host->code, where = d.st_host->where;
+        CK(h, cudaMemsetAsync(d.st, 0, 2 * sizeof(int32_t), d.stream));
+        CK(h, cudaStreamSynchronize(d.stream));
+        char buf[160];
+        if (code == ST_CAPACITY) {
+            snprintf(buf, sizeof buf, "particle at sorted position %d has more than max_contacts=%d contacts", where,
+                     d.maxc);
+            return fail(h, DEM_ERR_CAPACITY, buf);
+        }
+        snprintf(buf, sizeof buf, "non-finite position or velocity at sorted position %d", where);
+        return fail(h, DEM_ERR_NONFINITE, buf);
+    }
+    return DEM_OK;
+}
+
+dem_status rotate_counters(dem_handle* h) {
+    Domain& d = h->d;
+    CK(h, cudaMemcpyAsync(&d.st->last, &d.st->live, sizeof(CountersDev), cudaMemcpyDeviceToDevice, d.stream));
+    CK(h, cudaMemsetAsync(&d.st->live, 0, sizeof(CountersDev), d.stream));
+    return DEM_OK;
+}
+
+// Upload (or take from the device) particle arrays, build the grid and do the first sort.
+dem_status load_particles(dem_handle* h, int64_t n64, const double* x, const double* v, const double* w,
+                          const float* r, int where) {
+    Domain& d = h->d;
+    if (n64 < 0 || n64 > (int64_t)0x7FFFFF00) return fail(h, DEM_ERR_INVALID_ARG, "n out of range");
+    const uint32_t n = (uint32_t)n64;
+    if (where != DEM_HOST && where != DEM_DEVICE) return fail(h, DEM_ERR_INVALID_ARG, "where");
+    if (n > 0 && (!x || !v || !w || !r)) return fail(h, DEM_ERR_INVALID_ARG, "x, v, w and r are required");
+    // radii (and, for host input, positions) are checked on the host
+    std::vector<float> rh;
+    const float* rr = r;
+    if (n > 0 && where == DEM_DEVICE) {
+        rh.resize(n);
+        CK(h, cudaMemcpy(rh.data(), r, (size_t)n * 4, cudaMemcpyDeviceToHost));
+        rr = rh.data();
+    }
+    double rmax = 0.0;
+    for (uint32_t k = 0; k < n; ++k) {
+        if (!(rr[k] > 0.f) || !std::isfinite(rr[k])) return fail(h, DEM_ERR_INVALID_ARG, "radii must be finite and > 0");
+        rmax = std::max(rmax, (double)rr[k]);
+    }
+    if (where == DEM_HOST)
+        for (uint32_t k = 0; k < n; ++k)
+            if (!finite3(x + 3 * (size_t)k) || !finite3(v + 3 * (size_t)k) || !finite3(w + 3 * (size_t)k))
+                return fail(h, DEM_ERR_INVALID_ARG, "non-finite position, velocity or spin in the input");
+    // grid (Sec. 4.1): edge >= one diameter of the largest sphere (+ margin, + skin)
+    const dem_config& c = h->cfg;
+    const double hmin = 2.0 * rmax * (1.0 + std::ldexp(1.0, -10)) + c.skin;
+    double hc = c.cell_size > 0.0 ? c.cell_size : hmin;
+    if (n > 0 && hc < hmin * (1.0 - 1e-12))
+        return fail(h, DEM_ERR_INVALID_ARG, "cell_size is smaller than 2 r_max (1 + 2^-10) + skin");
+    if (n == 0 && !(hc > 0.0)) hc = 1.0;
+    int64_t nc = 1;
+    for (int a = 0; a < 3; ++a) {
+        h->origin[a] = c.domain_lo[a];
+        h->dims[a] = std::max<int64_t>(1, (int64_t)std::ceil((c.domain_hi[a] - c.domain_lo[a]) / hc));
+        nc *= h->dims[a];
+        if (nc > (int64_t)0x7FFFFFFF) return fail(h, DEM_ERR_INVALID_ARG, "grid has more than 2^31 cells");
+    }
+    h->h = hc;
+    h->rmax = rmax;
+    d.n = n;
+    d.ncells = (uint32_t)nc;
+    dem_status s = ensure_buffers(h, n, (uint32_t)nc);
+    if (s != DEM_OK) return s;
+    // scene table (one scene)
+    d.nscenes = 1;
+    d.h_scenes.assign(1, SceneDev{});
+    fill_scene(h, d.h_scenes[0], 0, n, 0);
+    if (!d.d_scenes) {
+        if (cudaMalloc(&d.d_scenes, sizeof(SceneDev)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, DEM_ERR_OOM, "cudaMalloc(scene table) failed");
+        }
+        d.scenes_cap = 1;
+    }
+    CK(h, cudaMemcpyAsync(d.d_scenes, d.h_scenes.data(), sizeof(SceneDev), cudaMemcpyHostToDevice, d.stream));
+    CK(h, cudaMemsetAsync(d.st, 0, sizeof(StatusDev), d.stream));
+    CK(h, cudaMemsetAsync(d.cnt, 0, ((size_t)d.ncells + 1) * 4, d.stream));
+    d.h_cur = 0;
+    if (n > 0) {
+        CK(h, cudaMemsetAsync(d.hcnt[0], 0, (size_t)n * 4, d.stream));
+        CK(h, cudaMemsetAsync(d.hcnt[1], 0, (size_t)n * 4, d.stream));
+        const double *xd = x, *vd = v, *wd = w;
+        const float* rd = r;
+        if (where == DEM_HOST) {
+            s = ensure_stage(h, n);
+            if (s != DEM_OK) return s;
+            CK(h, cudaMemcpyAsync(h->stage, x, (size_t)n * 24, cudaMemcpyHostToDevice, d.stream));
+            CK(h, cudaMemcpyAsync(h->stage + 3 * (size_t)n, v, (size_t)n * 24, cudaMemcpyHostToDevice, d.stream));
+            CK(h, cudaMemcpyAsync(h->stage + 6 * (size_t)n, w, (size_t)n * 24, cudaMemcpyHostToDevice, d.stream));
+            CK(h, cudaMemcpyAsync(h->stage_r, r, (size_t)n * 4, cudaMemcpyHostToDevice, d.stream));
+            xd = h->stage; vd = h->stage + 3 * (size_t)n; wd = h->stage + 6 * (size_t)n; rd = h->stage_r;
+        }
+        CK(h, run_import(d, xd, vd, wd, rd));
+        CK(h, run_hash_initial(d));
+        CK(h, run_rebuild(d));
+    }
+    h->has_particles = true;
+    h->eval_valid = false;
+    h->steps = 0;
+    return DEM_OK;
+}
+
+}  // namespace
+
+// =========================================================================== C ABI
+extern "C" {
+
+dem_status dem_create(const dem_config* cfg, int device, void* cuda_stream, dem_handle** out) {
+    if (!out) return DEM_ERR_INVALID_ARG;
+    *out = nullptr;
+    std::string why;
+    dem_status s = validate_config(cfg, why);
+    if (s != DEM_OK) return s;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return DEM_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(device);
+    dem_handle* h = new dem_handle();
+    h->cfg = *cfg;
+    h->device = device;
+    Domain& d = h->d;
+    d.precision = cfg->precision;
+    d.model = cfg->model;
+    d.stiffness = cfg->stiffness;
+    d.maxc = cfg->max_contacts > 0 ? cfg->max_contacts : 32;
+    d.block = cfg->block_size > 0 ? cfg->block_size : 128;
+    d.stream = (cudaStream_t)cuda_stream;
+    if (cudaMalloc(&d.st, sizeof(StatusDev)) != cudaSuccess ||
+        cudaMallocHost(&d.st_host, sizeof(StatusDev)) != cudaSuccess ||
+        cudaMalloc(&d.diag_out, 16 * sizeof(double)) != cudaSuccess ||
+        cudaMemset(d.st, 0, sizeof(StatusDev)) != cudaSuccess) {
+        cudaGetLastError();
+        dem_destroy(h);
+        return DEM_ERR_OOM;
+    }
+    *out = h;
+    return DEM_OK;
+}
+
+dem_status dem_set_particles(dem_handle* h, int64_t n, const uint32_t* id, const double* x, const double* v,
+                             const double* w, const float* r, int where) {
+    if (!h) return DEM_ERR_INVALID_ARG;
+    if (h->broken) return fail(h, DEM_ERR_STATE, "handle is unusable after a CUDA error");
+    if (id) return fail(h, DEM_ERR_INVALID_ARG, "id must be NULL (particle k has id k)");
+    DeviceGuard g(h->device);
+    dem_status s = load_particles(h, n, x, v, w, r, where);
+    if (s != DEM_OK) { h->has_particles = false; return s; }
+    CK(h, cudaStreamSynchronize(h->d.stream));
+    h->err.clear();
+    return DEM_OK;
+}
+
+dem_status dem_set_walls(dem_handle* h, int nwalls, const dem_wall* walls) {
+    if (!h) return DEM_ERR_INVALID_ARG;
+    if (h->broken) return fail(h, DEM_ERR_STATE, "handle is unusable after a CUDA error");
+    if (nwalls < 0 || nwalls > DEM_MAX_WALLS || (nwalls > 0 && !walls))
+        return fail(h, DEM_ERR_INVALID_ARG, "nwalls must be in [0, 8]");
+    for (int k = 0; k < nwalls; ++k) {
+        const dem_wall& w = walls[k];
+        if (w.kind != DEM_PLANE && w.kind != DEM_CYLINDER_IN) return fail(h, DEM_ERR_INVALID_ARG, "wall kind");
+        if (!finite3(w.p) || !finite3(w.n) || !finite3(w.omega) || !finite3(w.vel))
+            return fail(h, DEM_ERR_INVALID_ARG, "wall vectors must be finite");
+        const double nn = w.n[0] * w.n[0] + w.n[1] * w.n[1] + w.n[2] * w.n[2];
+        if (std::fabs(nn - 1.0) > 1e-12) return fail(h, DEM_ERR_INVALID_ARG, "wall n must be a unit vector");
+        if (w.kind == DEM_CYLINDER_IN) {
+            if (!(w.radius > 0.0)) return fail(h, DEM_ERR_INVALID_ARG, "cylinder radius must be > 0");
+            if (h->cfg.precision == DEM_FP32 && make_wall(w).axis < 0)
+                return fail(h, DEM_ERR_INVALID_ARG, "in DEM_FP32 mode a cylinder axis must be a coordinate axis");
+        }
+    }
+    DeviceGuard g(h->device);
+    h->walls.assign(walls, walls + nwalls);
+    if (h->has_particles && !h->d.h_scenes.empty()) {
+        Domain& d = h->d;
+        for (auto& S : d.h_scenes) {
+            S.nwalls = nwalls;
+            for (int k = 0; k < nwalls; ++k) S.walls[k] = make_wall(h->walls[k]);
+        }
+        CK(h, cudaMemcpyAsync(d.d_scenes, d.h_scenes.data(), sizeof(SceneDev) * d.h_scenes.size(),
+                              cudaMemcpyHostToDevice, d.stream));
+        CK(h, cudaStreamSynchronize(d.stream));
+    }
+    return DEM_OK;
+}
+
+dem_status dem_step(dem_handle* h, int64_t nsteps) {
+    if (!h) return DEM_ERR_INVALID_ARG;
+    if (h->broken) return fail(h, DEM_ERR_STATE, "handle is unusable after a CUDA error");
+    if (!h->has_particles) return fail(h, DEM_ERR_STATE, "dem_step before dem_set_particles");
+    if (nsteps < 0) return fail(h, DEM_ERR_INVALID_ARG, "nsteps < 0");
+    DeviceGuard g(h->device);
+    Domain& d = h->d;
+    const bool timed = h->timing && d.n > 0;
+    if (timed) {
+        const size_t need = 3 * (size_t)nsteps;
+        while (h->events.size() < need) {
+            cudaEvent_t e;
+            CK(h, cudaEventCreate(&e));
+            h->events.push_back(e);
+        }
+    }
+    for (int64_t s = 0; s < nsteps; ++s) {
+        if (timed) CK(h, cudaEventRecord(h->events[3 * s], d.stream));
+        CK(h, run_force(d, false, nullptr, nullptr));
+        if (timed) CK(h, cudaEventRecord(h->events[3 * s + 1], d.stream));
+        d.h_cur = 1 - d.h_cur;
+        CK(h, run_rebuild(d));
+        if (timed) CK(h, cudaEventRecord(h->events[3 * s + 2], d.stream));
+    }
+    h->steps += nsteps;
+    if (nsteps > 0) h->eval_valid = false;
+    dem_status st = sync_status(h);
+    if (timed) {
+        for (int64_t s = 0; s < nsteps; ++s) {
+            float a = 0.f, b = 0.f;
+            CK(h, cudaEventElapsedTime(&a, h->events[3 * s], h->events[3 * s + 1]));
+            CK(h, cudaEventElapsedTime(&b, h->events[3 * s + 1], h->events[3 * s + 2]));
+            h->t_force_ms += a;
+            h->t_sort_ms += b;
+        }
+        h->n_force += nsteps;
+        h->n_sort += nsteps;
+    }
+    return st;
+}
+
+dem_status dem_set_timing(dem_handle* h, int enable) {
+    if (!h) return DEM_ERR_INVALID_ARG;
+    h->timing = enable != 0;
+    if (h->timing) {
+        h->t_force_ms = h->t_sort_ms = 0.0;
+        h->n_force = h->n_sort = 0;
+    }
+    return DEM_OK;
+}
+
+dem_status dem_get_phase_times(const dem_handle* h, double* out) {
+    if (!h || !out) return DEM_ERR_INVALID_ARG;
+    out[0] = h->t_force_ms;
+    out[1] = h->t_sort_ms;
+    out[2] = (double)h->n_force;
+    out[3] = (double)h->n_sort;
+    return DEM_OK;
+}
+
+dem_status dem_get_state(dem_handle* h, double* x, double* v, double* w, int where) {
+    if (!h) return DEM_ERR_INVALID_ARG;
+    if (h->broken) return fail(h, DEM_ERR_STATE, "handle is unusable after a CUDA error");
+    if (!h->has_particles) return fail(h, DEM_ERR_STATE, "no particles");
+    if (where != DEM_HOST && where != DEM_DEVICE) return fail(h, DEM_ERR_INVALID_ARG, "where");
+    DeviceGuard g(h->device);
+    Domain& d = h->d;
+    const size_t n = d.n;
+    if (n == 0) return DEM_OK;
+    if (where == DEM_DEVICE) {
+        CK(h, run_export(d, x, v, w));
+    } else {
+        dem_status s = ensure_stage(h, d.n);
+        if (s != DEM_OK) return s;
+        CK(h, run_export(d, x ? h->stage : nullptr, v ? h->stage + 3 * n : nullptr, w ? h->stage + 6 * n : nullptr));
+        if (x) CK(h, cudaMemcpyAsync(x, h->stage, n * 24, cudaMemcpyDeviceToHost, d.stream));
+        if (v) CK(h, cudaMemcpyAsync(v, h->stage + 3 * n, n * 24, cudaMemcpyDeviceToHost, d.stream));
+        if (w) CK(h, cudaMemcpyAsync(w, h->stage + 6 * n, n * 24, cudaMemcpyDeviceToHost, d.stream));
+    }
+    CK(h, cudaStreamSynchronize(d.stream));
+    return DEM_OK;
+}
+
+dem_status dem_get_forces(dem_handle* h, double* F, double* T, int where) {
+    if (!h) return DEM_ERR_INVALID_ARG;
+    if (h->broken) return fail(h, DEM_ERR_STATE, "handle is unusable after a CUDA error");
+    if (!h->has_particles) return fail(h, DEM_ERR_STATE, "no particles");
+    if (where != DEM_HOST && where != DEM_DEVICE) return fail(h, DEM_ERR_INVALID_ARG, "where");
+    DeviceGuard g(h->device);
+    Domain& d = h->d;
+    const size_t n = d.n;
+    if (n == 0) return DEM_OK;
+    double *Fd = F, *Td = T;
+    if (where == DEM_HOST) {
+        dem_status s = ensure_stage(h, d.n);
+        if (s != DEM_OK) return s;
+        Fd = h->stage;
+        Td = h->stage + 3 * n;
+    }
+    CK(h, cudaMemsetAsync(&d.st->live, 0, sizeof(CountersDev), d.stream));
+    CK(h, run_force(d, true, Fd, Td));
+    dem_status s = rotate_counters(h);
+    if (s != DEM_OK) return s;
+    if (where == DEM_HOST) {
+        if (F) CK(h, cudaMemcpyAsync(F, Fd, n * 24, cudaMemcpyDeviceToHost, d.stream));
+        if (T) CK(h, cudaMemcpyAsync(T, Td, n * 24, cudaMemcpyDeviceToHost, d.stream));
+    }
+    h->eval_valid = true;
+    return sync_status(h);
+}
+
+static dem_status download_u32(dem_handle* h, std::vector<uint32_t>& out, const uint32_t* src, size_t count) {
+    out.resize(count);
+    if (count) CK(h, cudaMemcpyAsync(out.data(), src, count * 4, cudaMemcpyDeviceToHost, h->d.stream));
+    return DEM_OK;
+}
+
+dem_status dem_get_history(dem_handle* h, int64_t cap, uint32_t* oi, uint32_t* oj, double* od, int64_t* nout) {
+    if (!h || !nout || cap < 0) return DEM_ERR_INVALID_ARG;
+    if (h->broken) return fail(h, DEM_ERR_STATE, "handle is unusable after a CUDA error");
+    if (!h->has_particles) return fail(h, DEM_ERR_STATE, "no particles");
+    DeviceGuard g(h->device);
+    Domain& d = h->d;
+    const size_t n = d.n, N = d.cap, M = d.maxc;
+    *nout = 0;
+    if (n == 0 || d.model != 0) return DEM_OK;
+    std::vector<uint32_t> perm, ids, cnt;
+    dem_status s;
+    if ((s = download_u32(h, perm, d.perm, n)) != DEM_OK) return s;
+    if ((s = download_u32(h, ids, d.precision == 0 ? d.A64.id : d.A32.id, n)) != DEM_OK) return s;
+    if ((s = download_u32(h, cnt, d.hcnt[d.h_cur], N)) != DEM_OK) return s;
+    CK(h, cudaStreamSynchronize(d.stream));
+    uint32_t mx = 0;
+    for (size_t q = 0; q < n; ++q) mx = std::max(mx, std::min<uint32_t>(cnt[perm[q]], (uint32_t)M));
+    std::vector<uint32_t> pid((size_t)mx * N);
+    std::vector<double> dv((size_t)3 * mx * N);
+    if (mx) {
+        CK(h, cudaMemcpyAsync(pid.data(), d.hpid[d.h_cur], (size_t)mx * N * 4, cudaMemcpyDeviceToHost, d.stream));
+        for (int c = 0; c < 3; ++c) {
+            if (d.precision == 0) {
+                CK(h, cudaMemcpyAsync(dv.data() + (size_t)c * mx * N, (const double*)d.hd[d.h_cur] + (size_t)c * M * N,
+                                      (size_t)mx * N * 8, cudaMemcpyDeviceToHost, d.stream));
+            } else {
+                std::vector<float> tmp((size_t)mx * N);
+                CK(h, cudaMemcpyAsync(tmp.data(), (const float*)d.hd[d.h_cur] + (size_t)c * M * N, (size_t)mx * N * 4,
+                                      cudaMemcpyDeviceToHost, d.stream));
+                CK(h, cudaStreamSynchronize(d.stream));
+                for (size_t k = 0; k < tmp.size(); ++k) dv[(size_t)c * mx * N + k] = tmp[k];
+            }
+        }
+        CK(h, cudaStreamSynchronize(d.stream));
+    }
+    struct Rec { uint32_t i, j; double d[3]; };
+    std::vector<Rec> recs;
+    for (size_t q = 0; q < n; ++q) {
+        const uint32_t src = perm[q], owner = ids[q];
+        const uint32_t c = std::min<uint32_t>(cnt[src], (uint32_t)M);
+        for (uint32_t k = 0; k < c; ++k) {
+            const uint32_t p = pid[(size_t)k * N + src];
+            if (p >= DEM_WALL_BASE || owner < p) {
+                Rec r{owner, p, {dv[(size_t)0 * mx * N + (size_t)k * N + src], dv[(size_t)1 * mx * N + (size_t)k * N + src],
+                                 dv[(size_t)2 * mx * N + (size_t)k * N + src]}};
+                recs.push_back(r);
+            }
+        }
+    }
+    std::sort(recs.begin(), recs.end(), [](const Rec& a, const Rec& b) { return a.i != b.i ? a.i < b.i : a.j < b.j; });
+    *nout = (int64_t)recs.size();
+    for (size_t k = 0; k < recs.size() && (int64_t)k < cap; ++k) {
+        if (oi) oi[k] = recs[k].i;
+        if (oj) oj[k] = recs[k].j;
+        if (od) { od[3 * k] = recs[k].d[0]; od[3 * k + 1] = recs[k].d[1]; od[3 * k + 2] = recs[k].d[2]; }
+    }
+    return DEM_OK;
+}
+
+dem_status dem_restore(dem_handle* h, int64_t n, const double* x, const double* v, const double* w, const float* r,
+                       int64_t nrec, const uint32_t* ri, const uint32_t* rj, const double* rd) {
+    if (!h || nrec < 0 || (nrec > 0 && (!ri || !rj || !rd))) return DEM_ERR_INVALID_ARG;
+    if (h->broken) return fail(h, DEM_ERR_STATE, "handle is unusable after a CUDA error");
+    DeviceGuard g(h->device);
+    dem_status s = load_particles(h, n, x, v, w, r, DEM_HOST);
+    if (s != DEM_OK) { h->has_particles = false; return s; }
+    Domain& d = h->d;
+    if (nrec == 0 || d.model != 0) {
+        CK(h, cudaStreamSynchronize(d.stream));
+        return DEM_OK;
+    }
+    // per-particle lists in id order; after the first sort perm[q] is the id position
+    const size_t N = d.cap, M = d.maxc;
+    std::vector<uint32_t> cnt(N, 0), pid(M * N, 0);
+    std::vector<double> dv(3 * M * N, 0.0);
+    auto add = [&](uint32_t owner, uint32_t partner, double a, double b, double c) -> bool {
+        if (owner >= (uint32_t)n) return false;
+        const uint32_t k = cnt[owner];
+        if (k >= M) return false;
+        pid[(size_t)k * N + owner] = partner;
+        dv[(0 * M + k) * N + owner] = a;
+        dv[(1 * M + k) * N + owner] = b;
+        dv[(2 * M + k) * N + owner] = c;
+        cnt[owner] = k + 1;
+        return true;
+    };
+    const int nw = (int)h->walls.size();
+    for (int64_t k = 0; k < nrec; ++k) {
+        const uint32_t i = ri[k], j = rj[k];
+        const double* dd = rd + 3 * k;
+        bool ok;
+        if (j >= DEM_WALL_BASE) ok = (int)(j - DEM_WALL_BASE) < nw && add(i, j, dd[0], dd[1], dd[2]);
+        else ok = i < j && j < (uint32_t)n && add(i, j, dd[0], dd[1], dd[2]) && add(j, i, -dd[0], -dd[1], -dd[2]);
+        if (!ok) { h->has_particles = false; return fail(h, DEM_ERR_INVALID_ARG, "invalid or excess history record"); }
+    }
+    CK(h, cudaMemcpyAsync(d.hcnt[d.h_cur], cnt.data(), N * 4, cudaMemcpyHostToDevice, d.stream));
+    CK(h, cudaMemcpyAsync(d.hpid[d.h_cur], pid.data(), M * N * 4, cudaMemcpyHostToDevice, d.stream));
+    if (d.precision == 0) {
+        CK(h, cudaMemcpyAsync(d.hd[d.h_cur], dv.data(), 3 * M * N * 8, cudaMemcpyHostToDevice, d.stream));
+        CK(h, cudaStreamSynchronize(d.stream));
+    } else {
+        std::vector<float> f(dv.size());
+        for (size_t k = 0; k < dv.size(); ++k) f[k] = (float)dv[k];
+        CK(h, cudaMemcpyAsync(d.hd[d.h_cur], f.data(), f.size() * 4, cudaMemcpyHostToDevice, d.stream));
+        CK(h, cudaStreamSynchronize(d.stream));
+    }
+    return DEM_OK;
+}
+
+dem_status dem_get_diagnostics(dem_handle* h, double* out) {
+    if (!h || !out) return DEM_ERR_INVALID_ARG;
+    if (h->broken) return fail(h, DEM_ERR_STATE, "handle is unusable after a CUDA error");
+    if (!h->has_particles) return fail(h, DEM_ERR_STATE, "no particles");
+    DeviceGuard g(h->device);
+    Domain& d = h->d;
+    CK(h, run_diag(d));
+    double tmp[10];
+    CK(h, cudaMemcpyAsync(tmp, d.diag_out, 10 * sizeof(double), cudaMemcpyDeviceToHost, d.stream));
+    CK(h, cudaMemcpyAsync(d.st_host, d.st, sizeof(StatusDev), cudaMemcpyDeviceToHost, d.stream));
+    CK(h, cudaStreamSynchronize(d.stream));
+    for (int k = 0; k < 10; ++k) out[k] = tmp[k];
+    const CountersDev& c = d.st_host->last;
+    float mo;
+    std::memcpy(&mo, &c.max_overlap_bits, 4);
+    out[10] = (double)c.ncontacts / 2.0;
+    out[11] = (double)c.nwallc;
+    out[12] = (double)mo;
+    out[13] = (double)h->steps;
+    out[14] = (double)d.sorts;
+    out[15] = (double)c.clamped;
+    return DEM_OK;
+}
+
+dem_status dem_debug_snapshot(dem_handle* h, uint32_t* cell, uint32_t* order, int64_t pair_cap, uint32_t* pairs,
+                              int64_t* npairs) {
+    if (!h) return DEM_ERR_INVALID_ARG;
+    if (h->broken) return fail(h, DEM_ERR_STATE, "handle is unusable after a CUDA error");
+    if (!h->has_particles) return fail(h, DEM_ERR_STATE, "no particles");
+    DeviceGuard g(h->device);
+    Domain& d = h->d;
+    const size_t n = d.n, N = d.cap;
+    std::vector<uint32_t> ids, skey;
+    dem_status s;
+    if ((s = download_u32(h, ids, d.precision == 0 ? d.A64.id : d.A32.id, n)) != DEM_OK) return s;
+    if ((s = download_u32(h, skey, d.skey, n)) != DEM_OK) return s;
+    CK(h, cudaStreamSynchronize(d.stream));
+    if (cell)
+        for (size_t q = 0; q < n; ++q) cell[ids[q]] = skey[q];
+    if (order)
+        for (size_t q = 0; q < n; ++q) order[q] = ids[q];
+    if (npairs) *npairs = 0;
+    if (pairs || npairs) {
+        if (!h->eval_valid) return fail(h, DEM_ERR_STATE, "pairs need a dem_get_forces call on the current state");
+        const int ho = 1 - d.h_cur;
+        std::vector<uint32_t> cnt;
+        if ((s = download_u32(h, cnt, d.hcnt[ho], n)) != DEM_OK) return s;
+        CK(h, cudaStreamSynchronize(d.stream));
+        uint32_t mx = 0;
+        for (size_t q = 0; q < n; ++q) mx = std::max(mx, std::min<uint32_t>(cnt[q], (uint32_t)d.maxc));
+        std::vector<uint32_t> pid((size_t)mx * N);
+        if (mx) {
+            CK(h, cudaMemcpyAsync(pid.data(), d.hpid[ho], (size_t)mx * N * 4, cudaMemcpyDeviceToHost, d.stream));
+            CK(h, cudaStreamSynchronize(d.stream));
+        }
+        std::vector<std::pair<uint32_t, uint32_t>> pr;
+        for (size_t q = 0; q < n; ++q) {
+            const uint32_t c = std::min<uint32_t>(cnt[q], (uint32_t)d.maxc);
+            for (uint32_t k = 0; k < c; ++k) {
+                const uint32_t p = pid[(size_t)k * N + q];
+                if (p < DEM_WALL_BASE && ids[q] < p) pr.emplace_back(ids[q], p);
+            }
+        }
+        std::sort(pr.begin(), pr.end());
+        if (npairs) *npairs = (int64_t)pr.size();
+        if (pairs)
+            for (size_t k = 0; k < pr.size() && (int64_t)k < pair_cap; ++k) {
+                pairs[2 * k] = pr[k].first;
+                pairs[2 * k + 1] = pr[k].second;
+            }
+    }
+    return DEM_OK;
+}
+
+dem_status dem_get_grid(const dem_handle* h, double* origin, double* cell, int64_t* dims) {
+    if (!h) return DEM_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a) {
+        if (origin) origin[a] = h->origin[a];
+        if (dims) dims[a] = h->dims[a];
+    }
+    if (cell) *cell = h->h;
+    return DEM_OK;
+}
+
+int64_t dem_device_bytes(const dem_handle* h) {
+    if (!h) return 0;
+    const Domain& d = h->d;
+    const size_t N = d.cap, M = d.maxc, C = (size_t)d.cells_cap + 1;
+    const size_t T = d.precision == 0 ? 8 : 4;
+    size_t state = d.precision == 0 ? N * (9 * 8 + 8) : N * (4 * 16 + 4);
+    size_t b = 2 * state + 2 * (N * 4 + N * 4 * M + N * T * 3 * M) + 5 * N * 4 + 2 * C * 4 + (size_t)d.part_cap * 4 +
+               (size_t)d.diag_part_cap * 80 + sizeof(StatusDev) + 128 + sizeof(SceneDev) * d.scenes_cap;
+    b += (size_t)h->stage_cap * (9 * 8 + 4);
+    return (int64_t)b;
+}
+
+int64_t dem_launch_count(const dem_handle* h) { return h ? h->d.launches : 0; }
+
+const char* dem_last_error(const dem_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+void dem_destroy(dem_handle* h) {
+    if (!h) return;
+    DeviceGuard g(h->device);
+    if (h->d.stream) cudaStreamSynchronize(h->d.stream);
+    else cudaDeviceSynchronize();
+    free_particle_buffers(h->d);
+    if (h->d.d_scenes) cudaFree(h->d.d_scenes);
+    if (h->d.st) cudaFree(h->d.st);
+    if (h->d.st_host) cudaFreeHost(h->d.st_host);
+    if (h->d.diag_out) cudaFree(h->d.diag_out);
+    if (h->stage) cudaFree(h->stage);
+    if (h->stage_r) cudaFree(h->stage_r);
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    cudaGetLastError();
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,938 @@
+// Kernels of the GB300 DEM timestep and their launchers.
+//
+//   k_force      steps 5-8 + 1 + 2: 27-cell contact search (Eq. 12), contact laws
+//                (Eq. 1 or Eqs. 2-10), walls, gravity, semi-implicit Euler, new cell key
+//                CM and its rank within the cell (one thread per cell-sorted particle)
+//   k_scan_*     exclusive scan of per-cell counts -> dense cell-start table
+//   k_scatter    particles into cell-major slots (order within a cell still arbitrary)
+//   k_reorder    step 4: (cell, id) order (Eq. 11) and gather of every property
+//   k_import / k_export / k_hash_initial / k_diag*   set-up, read-out, diagnostics
+#include <cuda_runtime.h>
+
+#include "dem_domain.h"
+
+namespace demgb {
+
+// ======================================================================= FP64 policy
+struct PF64 {
+    using T = double;
+    using State = StateF64;
+    struct Self {
+        double x, y, z;
+        float r;
+        V3<double> v, w;
+        uint32_t id;
+    };
+    static __device__ __forceinline__ Self load(const State& s, uint32_t q) {
+        Self m;
+        m.x = s.x[q]; m.y = s.y[q]; m.z = s.z[q];
+        m.r = s.r[q];
+        m.v = mk(s.vx[q], s.vy[q], s.vz[q]);
+        m.w = mk(s.wx[q], s.wy[q], s.wz[q]);
+        m.id = s.id[q];
+        return m;
+    }
+    static __device__ __forceinline__ void store(const State& s, uint32_t q, const Self& m) {
+        s.x[q] = m.x; s.y[q] = m.y; s.z[q] = m.z;
+        s.r[q] = m.r;
+        s.vx[q] = m.v.x; s.vy[q] = m.v.y; s.vz[q] = m.v.z;
+        s.wx[q] = m.w.x; s.wy[q] = m.w.y; s.wz[q] = m.w.z;
+        s.id[q] = m.id;
+    }
+    static __device__ __forceinline__ void load_vw(const State& s, uint32_t j, V3<double>& v, V3<double>& w) {
+        v = mk(__ldg(&s.vx[j]), __ldg(&s.vy[j]), __ldg(&s.vz[j]));
+        w = mk(__ldg(&s.wx[j]), __ldg(&s.wy[j]), __ldg(&s.wz[j]));
+    }
+    // Contact iff d^2 < R^2 with d^2 = fma(dz,dz, fma(dy,dy, dx*dx)), R = r_i + r_j (exact).
+    static __device__ __forceinline__ bool contact(const State& s, const Self& me, uint32_t j, const SceneDev&,
+                                                   V3<double>& n, double& delta, float& rj) {
+        const double dx = __dsub_rn(__ldg(&s.x[j]), me.x);
+        const double dy = __dsub_rn(__ldg(&s.y[j]), me.y);
+        const double dz = __dsub_rn(__ldg(&s.z[j]), me.z);
+        const float rjf = __ldg(&s.r[j]);
+        const double d2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+        const double R = __dadd_rn((double)me.r, (double)rjf);
+        if (!(d2 < __dmul_rn(R, R))) return false;
+        const double d = sqrt(d2);
+        n = mk(dx / d, dy / d, dz / d);
+        delta = R - d;
+        rj = rjf;
+        return true;
+    }
+    // Wall geometry: n from the sphere toward the wall, overlap, and c - p (contact point
+    // relative to the wall's reference point).
+    static __device__ __forceinline__ bool wall(const WallDev& W, const Self& me, const SceneDev&, V3<double>& n,
+                                                double& delta, V3<double>& cp) {
+        const V3<double> x = mk(me.x, me.y, me.z);
+        const V3<double> p = mk(W.p[0], W.p[1], W.p[2]);
+        const V3<double> a = mk(W.n[0], W.n[1], W.n[2]);
+        const double r = (double)me.r;
+        if (W.kind == 0) {
+            const double s = dot(x - p, a);
+            const double d = r - s;
+            if (!(d > 0.0)) return false;
+            n = a * -1.0;
+            delta = d;
+            cp = (x - a * s) - p;
+            return true;
+        }
+        const V3<double> q = x - p;
+        const double ax = dot(q, a);
+        const V3<double> rho = q - a * ax;
+        const double rr = sqrt(dot(rho, rho));
+        const double d = rr + r - W.radius;
+        if (!(d > 0.0) || !(rr > 0.0)) return false;
+        n = rho * (1.0 / rr);
+        delta = d;
+        cp = a * ax + n * W.radius;
+        return true;
+    }
+    static __device__ __forceinline__ V3<double> wall_vel(const WallDev& W, V3<double> cp) {
+        return mk(W.vel[0], W.vel[1], W.vel[2]) + cross(mk(W.omega[0], W.omega[1], W.omega[2]), cp);
+    }
+    static __device__ __forceinline__ double mass(const SceneDev& S, float r) {
+        const double rd = (double)r;
+        return S.cmass * rd * rd * rd;
+    }
+    static __device__ __forceinline__ uint32_t axis_cell(const SceneDev& S, int a, double xa, bool& clamped) {
+        const double c = floor(__ddiv_rn(__dsub_rn(xa, S.origin[a]), S.h));
+        if (!(c >= 0.0)) { clamped = true; return 0; }
+        if (c >= (double)S.dims[a]) { clamped = true; return (uint32_t)(S.dims[a] - 1); }
+        return (uint32_t)c;
+    }
+    static __device__ __forceinline__ uint32_t cell_key(const SceneDev& S, double x, double y, double z, bool& clamped) {
+        const uint32_t i = axis_cell(S, 0, x, clamped), j = axis_cell(S, 1, y, clamped), k = axis_cell(S, 2, z, clamped);
+        return S.c0 + (k * (uint32_t)S.dims[1] + j) * (uint32_t)S.dims[0] + i;
+    }
+    static __device__ __forceinline__ uint32_t key_of(const State& s, const SceneDev& S, uint32_t q, bool& clamped) {
+        return cell_key(S, s.x[q], s.y[q], s.z[q], clamped);
+    }
+    // Semi-implicit Euler (Sec. 4.2 step 1): v' = v + F dt/m, w' = w + T dt/I, x' = x + v' dt.
+    static __device__ __forceinline__ uint32_t integrate(const State& B, uint32_t q, const Self& me, V3<double> F,
+                                                         V3<double> Tq, const SceneDev& S, double m, bool& clamped,
+                                                         bool& finite) {
+        const double r = (double)me.r;
+        const double I = 0.4 * m * r * r;
+        const V3<double> vn = me.v + F * (S.dt / m);
+        const V3<double> wn = me.w + Tq * (S.dt / I);
+        const double xn = me.x + vn.x * S.dt, yn = me.y + vn.y * S.dt, zn = me.z + vn.z * S.dt;
+        B.x[q] = xn; B.y[q] = yn; B.z[q] = zn;
+        B.r[q] = me.r;
+        B.vx[q] = vn.x; B.vy[q] = vn.y; B.vz[q] = vn.z;
+        B.wx[q] = wn.x; B.wy[q] = wn.y; B.wz[q] = wn.z;
+        B.id[q] = me.id;
+        finite = isfinite(xn) && isfinite(yn) && isfinite(zn) && isfinite(vn.x) && isfinite(vn.y) && isfinite(vn.z);
+        return cell_key(S, xn, yn, zn, clamped);
+    }
+    static __device__ __forceinline__ V3<double> pos(const Self& m) { return mk(m.x, m.y, m.z); }
+    static __device__ __forceinline__ V3<double> vel(const Self& m) { return m.v; }
+    static __device__ __forceinline__ V3<double> spin(const Self& m) { return m.w; }
+};
+
+// ======================================================================= FP32 policy
+// Positions are hi + lo (two floats per coordinate, hi = fl32(hi + lo)).
+__device__ __forceinline__ void ff_diff(float hi, float lo, float phi, float plo, float& u, float& ul) {
+    float e;
+    two_sum(hi, -phi, u, e);
+    ul = __fadd_rn(__fsub_rn(lo, plo), e);
+}
+
+struct PF32 {
+    using T = float;
+    using State = StateF32;
+    struct Self {
+        float hx, hy, hz, r, lx, ly, lz;
+        V3<float> v, w;
+        uint32_t id;
+    };
+    static __device__ __forceinline__ Self load(const State& s, uint32_t q) {
+        Self m;
+        const float4 p0 = s.P0[q], p1 = s.P1[q], v = s.V[q], w = s.W[q];
+        m.hx = p0.x; m.hy = p0.y; m.hz = p0.z; m.r = p0.w;
+        m.lx = p1.x; m.ly = p1.y; m.lz = p1.z;
+        m.v = mk(v.x, v.y, v.z);
+        m.w = mk(w.x, w.y, w.z);
+        m.id = s.id[q];
+        return m;
+    }
+    static __device__ __forceinline__ void store(const State& s, uint32_t q, const Self& m) {
+        s.P0[q] = make_float4(m.hx, m.hy, m.hz, m.r);
+        s.P1[q] = make_float4(m.lx, m.ly, m.lz, 0.f);
+        s.V[q] = make_float4(m.v.x, m.v.y, m.v.z, 0.f);
+        s.W[q] = make_float4(m.w.x, m.w.y, m.w.z, 0.f);
+        s.id[q] = m.id;
+    }
+    static __device__ __forceinline__ void load_vw(const State& s, uint32_t j, V3<float>& v, V3<float>& w) {
+        const float4 a = __ldg(&s.V[j]), b = __ldg(&s.W[j]);
+        v = mk(a.x, a.y, a.z);
+        w = mk(b.x, b.y, b.z);
+    }
+    // FP32 prefilter on hi (conservative by eps_f), then the sign of R^2 - d^2 evaluated
+    // with error-free transformations (about 2^-46 relative to R^2).
+    static __device__ __forceinline__ bool contact(const State& s, const Self& me, uint32_t j, const SceneDev& S,
+                                                   V3<float>& n, float& delta, float& rj) {
+        const float4 pj = __ldg(&s.P0[j]);
+        const float ax = pj.x - me.hx, ay = pj.y - me.hy, az = pj.z - me.hz;
+        const float Re = (pj.w + me.r) + S.eps_f;
+        if (ax * ax + ay * ay + az * az >= Re * Re) return false;
+        const float4 lj = __ldg(&s.P1[j]);
+        float sx, tx, sy, ty, sz, tz;
+        ff_diff(pj.x, lj.x, me.hx, me.lx, sx, tx);
+        ff_diff(pj.y, lj.y, me.hy, me.ly, sy, ty);
+        ff_diff(pj.z, lj.z, me.hz, me.lz, sz, tz);
+        float px, pex, py, pey, pz, pez;
+        two_prod(sx, sx, px, pex);
+        two_prod(sy, sy, py, pey);
+        two_prod(sz, sz, pz, pez);
+        float Rh, Rl;
+        two_sum(me.r, pj.w, Rh, Rl);
+        float qh, qe;
+        two_prod(Rh, Rh, qh, qe);
+        float a1, e1, a2, e2, a3, e3;
+        two_sum(qh, -px, a1, e1);
+        two_sum(a1, -py, a2, e2);
+        two_sum(a2, -pz, a3, e3);
+        const float cx = __fmaf_rn(2.f * sx, tx, __fmul_rn(tx, tx));
+        const float cy = __fmaf_rn(2.f * sy, ty, __fmul_rn(ty, ty));
+        const float cz = __fmaf_rn(2.f * sz, tz, __fmul_rn(tz, tz));
+        const float rr = __fmaf_rn(2.f * Rh, Rl, __fmul_rn(Rl, Rl));
+        float low = __fadd_rn(__fadd_rn(e1, e2), e3);
+        low = __fadd_rn(low, __fadd_rn(qe, rr));
+        low = __fsub_rn(low, __fadd_rn(__fadd_rn(pex, pey), pez));
+        low = __fsub_rn(low, __fadd_rn(__fadd_rn(cx, cy), cz));
+        const float D = __fadd_rn(a3, low);
+        if (!(D > 0.f)) return false;
+        const float d = sqrtf(__fadd_rn(__fadd_rn(px, py), pz));
+        delta = __fdiv_rn(D, __fadd_rn(Rh, d));
+        const float dc = __fadd_rn(__fsub_rn(Rh, delta), Rl);
+        const float inv = __fdiv_rn(1.f, dc);
+        n = mk(__fmul_rn(__fadd_rn(sx, tx), inv), __fmul_rn(__fadd_rn(sy, ty), inv), __fmul_rn(__fadd_rn(sz, tz), inv));
+        rj = pj.w;
+        return true;
+    }
+    static __device__ __forceinline__ float hic(const Self& m, int a) { return a == 0 ? m.hx : (a == 1 ? m.hy : m.hz); }
+    static __device__ __forceinline__ float loc(const Self& m, int a) { return a == 0 ? m.lx : (a == 1 ? m.ly : m.lz); }
+    static __device__ __forceinline__ bool wall(const WallDev& W, const Self& me, const SceneDev& S, V3<float>& n,
+                                                float& delta, V3<float>& cp) {
+        const float r = me.r;
+        if (W.kind == 0) {
+            // prefilter: centre farther than r + eps from the plane
+            const float sf = W.nf[0] * (me.hx - W.pf[0]) + W.nf[1] * (me.hy - W.pf[1]) + W.nf[2] * (me.hz - W.pf[2]);
+            if (sf >= r + S.eps_f) return false;
+            float u[3], ul[3];
+            for (int a = 0; a < 3; ++a) ff_diff(hic(me, a), loc(me, a), W.p_hi[a], W.p_lo[a], u[a], ul[a]);
+            float sh, sl;
+            if (W.axis >= 0) {
+                const float sg = W.n_hi[W.axis];
+                sh = u[W.axis] * sg;
+                sl = ul[W.axis] * sg;
+            } else {
+                float m0, e0, m1, e1, m2, e2;
+                two_prod(W.n_hi[0], u[0], m0, e0);
+                two_prod(W.n_hi[1], u[1], m1, e1);
+                two_prod(W.n_hi[2], u[2], m2, e2);
+                float s01, f01, s012, f012;
+                two_sum(m0, m1, s01, f01);
+                two_sum(s01, m2, s012, f012);
+                float lw = __fadd_rn(__fadd_rn(e0, e1), e2);
+                lw = __fadd_rn(lw, __fadd_rn(f01, f012));
+                for (int a = 0; a < 3; ++a)
+                    lw = __fadd_rn(lw, __fadd_rn(__fmul_rn(W.n_hi[a], ul[a]), __fmul_rn(W.n_lo[a], u[a])));
+                sh = s012;
+                sl = lw;
+            }
+            float dh, de;
+            two_sum(r, -sh, dh, de);
+            const float d = __fadd_rn(dh, __fsub_rn(de, sl));
+            if (!(d > 0.f)) return false;
+            n = mk(-W.nf[0], -W.nf[1], -W.nf[2]);
+            delta = d;
+            const float s = __fadd_rn(sh, sl);
+            cp = mk((u[0] + ul[0]) - s * W.nf[0], (u[1] + ul[1]) - s * W.nf[1], (u[2] + ul[2]) - s * W.nf[2]);
+            return true;
+        }
+        // cylinder interior with a coordinate axis
+        const int ax = W.axis, b = (ax + 1) % 3, c = (ax + 2) % 3;
+        const float gf = W.rad_hi - r;
+        {
+            const float ub = hic(me, b) - W.pf[b], uc = hic(me, c) - W.pf[c];
+            const float lim = gf - S.eps_f;
+            if (lim > 0.f && ub * ub + uc * uc <= lim * lim) return false;
+        }
+        float ub, ubl, uc, ucl;
+        ff_diff(hic(me, b), loc(me, b), W.p_hi[b], W.p_lo[b], ub, ubl);
+        ff_diff(hic(me, c), loc(me, c), W.p_hi[c], W.p_lo[c], uc, ucl);
+        float pb, peb, pc, pec;
+        two_prod(ub, ub, pb, peb);
+        two_prod(uc, uc, pc, pec);
+        float s1, e1;
+        two_sum(pb, pc, s1, e1);
+        float rlo = __fadd_rn(e1, __fadd_rn(peb, pec));
+        rlo = __fadd_rn(rlo, __fadd_rn(__fmaf_rn(2.f * ub, ubl, __fmul_rn(ubl, ubl)),
+                                       __fmaf_rn(2.f * uc, ucl, __fmul_rn(ucl, ucl))));
+        float g, ge;
+        two_sum(W.rad_hi, -r, g, ge);
+        const float gl = __fadd_rn(ge, W.rad_lo);
+        float gg, gge;
+        two_prod(g, g, gg, gge);
+        const float glo = __fadd_rn(gge, __fmaf_rn(2.f * g, gl, __fmul_rn(gl, gl)));
+        float a, ae;
+        two_sum(s1, -gg, a, ae);
+        const float D = __fadd_rn(a, __fadd_rn(ae, __fsub_rn(rlo, glo)));
+        if (!(D > 0.f)) return false;
+        const float rho = sqrtf(s1);
+        if (!(rho > 0.f)) return false;
+        delta = __fdiv_rn(D, __fadd_rn(rho, g));
+        const float rc = __fadd_rn(__fadd_rn(g, gl), delta);
+        const float inv = __fdiv_rn(1.f, rc);
+        float nn[3];
+        nn[ax] = 0.f;
+        nn[b] = __fmul_rn(__fadd_rn(ub, ubl), inv);
+        nn[c] = __fmul_rn(__fadd_rn(uc, ucl), inv);
+        n = mk(nn[0], nn[1], nn[2]);
+        float cpp[3];
+        cpp[ax] = hic(me, ax) - W.pf[ax] + (loc(me, ax) - W.p_lo[ax]);
+        cpp[b] = W.rad_hi * nn[b];
+        cpp[c] = W.rad_hi * nn[c];
+        cp = mk(cpp[0], cpp[1], cpp[2]);
+        return true;
+    }
+    static __device__ __forceinline__ V3<float> wall_vel(const WallDev& W, V3<float> cp) {
+        return mk(W.velf[0], W.velf[1], W.velf[2]) + cross(mk(W.omegaf[0], W.omegaf[1], W.omegaf[2]), cp);
+    }
+    static __device__ __forceinline__ float mass(const SceneDev& S, float r) { return S.cmass_f * (r * r * r); }
+    static __device__ __forceinline__ uint32_t axis_cell(const SceneDev& S, int a, float hi, bool& clamped) {
+        const float c = floorf(__fdiv_rn(__fsub_rn(hi, S.origin_f[a]), S.h_f));
+        if (!(c >= 0.f)) { clamped = true; return 0; }
+        if (c >= (float)S.dims[a]) { clamped = true; return (uint32_t)(S.dims[a] - 1); }
+        return (uint32_t)c;
+    }
+    static __device__ __forceinline__ uint32_t cell_key(const SceneDev& S, float x, float y, float z, bool& clamped) {
+        const uint32_t i = axis_cell(S, 0, x, clamped), j = axis_cell(S, 1, y, clamped), k = axis_cell(S, 2, z, clamped);
+        return S.c0 + (k * (uint32_t)S.dims[1] + j) * (uint32_t)S.dims[0] + i;
+    }
+    static __device__ __forceinline__ uint32_t key_of(const State& s, const SceneDev& S, uint32_t q, bool& clamped) {
+        const float4 p = s.P0[q];
+        return cell_key(S, p.x, p.y, p.z, clamped);
+    }
+    // position += dt * v' with compensated summation: TwoSum(hi, dx), lo += err, renormalise
+    static __device__ __forceinline__ void advance(float& hi, float& lo, float dx) {
+        float s, e;
+        two_sum(hi, dx, s, e);
+        const float l2 = __fadd_rn(lo, e);
+        two_sum(s, l2, hi, lo);
+    }
+    static __device__ __forceinline__ uint32_t integrate(const State& B, uint32_t q, const Self& me, V3<float> F,
+                                                         V3<float> Tq, const SceneDev& S, float m, bool& clamped,
+                                                         bool& finite) {
+        const float r = me.r;
+        const float I = 0.4f * m * r * r;
+        const V3<float> vn = me.v + F * (S.dt_f / m);
+        const V3<float> wn = me.w + Tq * (S.dt_f / I);
+        float hx = me.hx, hy = me.hy, hz = me.hz, lx = me.lx, ly = me.ly, lz = me.lz;
+        advance(hx, lx, __fmul_rn(vn.x, S.dt_f));
+        advance(hy, ly, __fmul_rn(vn.y, S.dt_f));
+        advance(hz, lz, __fmul_rn(vn.z, S.dt_f));
+        B.P0[q] = make_float4(hx, hy, hz, r);
+        B.P1[q] = make_float4(lx, ly, lz, 0.f);
+        B.V[q] = make_float4(vn.x, vn.y, vn.z, 0.f);
+        B.W[q] = make_float4(wn.x, wn.y, wn.z, 0.f);
+        B.id[q] = me.id;
+        finite = isfinite(hx) && isfinite(hy) && isfinite(hz) && isfinite(vn.x) && isfinite(vn.y) && isfinite(vn.z);
+        return cell_key(S, hx, hy, hz, clamped);
+    }
+    static __device__ __forceinline__ V3<double> pos(const Self& m) {
+        return mk((double)m.hx + (double)m.lx, (double)m.hy + (double)m.ly, (double)m.hz + (double)m.lz);
+    }
+    static __device__ __forceinline__ V3<double> vel(const Self& m) { return mk((double)m.v.x, (double)m.v.y, (double)m.v.z); }
+    static __device__ __forceinline__ V3<double> spin(const Self& m) { return mk((double)m.w.x, (double)m.w.y, (double)m.w.z); }
+};
+
+// ======================================================================= force pass
+template <class PR>
+struct ForceArgs {
+    const SceneDev* scenes;
+    int nscenes;
+    uint32_t n, cap;
+    int maxc, stiffness;
+    typename PR::State A, B;
+    const uint32_t* skey;
+    const uint32_t* cs;
+    const uint32_t* perm;
+    const uint32_t* hin_cnt;
+    const uint32_t* hin_pid;
+    const typename PR::T* hin_d;
+    uint32_t* hout_cnt;
+    uint32_t* hout_pid;
+    typename PR::T* hout_d;
+    uint32_t* key;
+    uint32_t* rank;
+    uint32_t* cnt;
+    StatusDev* st;
+    double* dbgF;
+    double* dbgT;
+};
+
+template <class PR, int MODEL, bool EVAL>
+__global__ void __launch_bounds__(256) k_force(ForceArgs<PR> a) {
+    using T = typename PR::T;
+    extern __shared__ uint32_t s_oid[];   // [maxc][blockDim.x]: partner ids of the stored springs
+    const uint32_t tid = threadIdx.x;
+    const uint32_t bd = blockDim.x;
+    const uint32_t q = blockIdx.x * bd + tid;
+    uint32_t c_pp = 0, c_wc = 0, c_clamp = 0, c_nnew = 0;
+    float c_maxov = 0.f;
+    if (q < a.n) {
+        const int si = scene_of(a.scenes, a.nscenes, q);
+        const SceneDev& S = a.scenes[si];
+        const typename PR::Self me = PR::load(a.A, q);
+        const uint32_t src = a.perm ? a.perm[q] : q;
+        const size_t cap = a.cap;
+        const int maxc = a.maxc;
+        uint32_t cnt_old = 0;
+        if (MODEL == 0 || !S.active) {
+            cnt_old = min(a.hin_cnt[src], (uint32_t)maxc);
+            for (uint32_t k = 0; k < cnt_old; ++k) s_oid[k * bd + tid] = a.hin_pid[k * cap + src];
+        }
+        if (!S.active) {
+            // frozen scene: carry state and springs unchanged
+            if (!EVAL) {
+                PR::store(a.B, q, me);
+                for (uint32_t k = 0; k < cnt_old; ++k) {
+                    a.hout_pid[k * cap + q] = s_oid[k * bd + tid];
+                    for (int c = 0; c < 3; ++c)
+                        a.hout_d[(c * (size_t)maxc + k) * cap + q] = a.hin_d[(c * (size_t)maxc + k) * cap + src];
+                }
+                a.hout_cnt[q] = cnt_old;
+                const uint32_t kk = a.skey[q];
+                a.key[q] = kk;
+                a.rank[q] = atomicAdd(&a.cnt[kk], 1u);
+            } else {
+                a.hout_cnt[q] = 0;
+            }
+        } else {
+            const Law<T> L = law_of(S, a.stiffness, T());
+            const T mi = PR::mass(S, me.r);
+            const T ri = (T)me.r;
+            const int nx = S.dims[0], ny = S.dims[1], nz = S.dims[2];
+            const uint32_t local = a.skey[q] - S.c0;
+            const int ix = (int)(local % (uint32_t)nx);
+            const uint32_t t1 = local / (uint32_t)nx;
+            const int iy = (int)(t1 % (uint32_t)ny);
+            const int iz = (int)(t1 / (uint32_t)ny);
+            V3<T> F = mk(T(0), T(0), T(0)), Tq = mk(T(0), T(0), T(0));
+            uint32_t nnew = 0;
+            // ---- particle-particle contacts: 27 cells (Eq. 12), as 9 rows of 3 contiguous cells
+            for (int dz = -1; dz <= 1; ++dz) {
+                const int z2 = iz + dz;
+                if (z2 < 0 || z2 >= nz) continue;
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int y2 = iy + dy;
+                    if (y2 < 0 || y2 >= ny) continue;
+                    const uint32_t rowbase = S.c0 + (uint32_t)((z2 * ny + y2) * nx);
+                    const uint32_t clo = rowbase + (uint32_t)max(ix - 1, 0);
+                    const uint32_t chi = rowbase + (uint32_t)min(ix + 1, nx - 1);
+                    const uint32_t j0 = __ldg(&a.cs[clo]), j1 = __ldg(&a.cs[chi + 1]);
+                    for (uint32_t j = j0; j < j1; ++j) {
+                        if (j == q) continue;
+                        V3<T> n;
+                        T delta;
+                        float rj;
+                        if (!PR::contact(a.A, me, j, S, n, delta, rj)) continue;
+                        const uint32_t gid = __ldg(&a.A.id[j]);
+                        V3<T> vj, wj;
+                        PR::load_vw(a.A, j, vj, wj);
+                        const V3<T> v = me.v - vj;
+                        if (MODEL == 0) {
+                            const T rjT = (T)rj;
+                            const V3<T> rw = mk(sym_madd(ri, me.w.x, rjT, wj.x), sym_madd(ri, me.w.y, rjT, wj.y),
+                                                sym_madd(ri, me.w.z, rjT, wj.z));
+                            const T mj = PR::mass(S, rj);
+                            const T meff = T(1) / (T(1) / mi + T(1) / mj);
+                            const T Reff = T(1) / (T(1) / ri + T(1) / rjT);
+                            V3<T> dold = mk(T(0), T(0), T(0));
+                            for (uint32_t k = 0; k < cnt_old; ++k)
+                                if (s_oid[k * bd + tid] == gid) {
+                                    dold = mk(a.hin_d[(0 * (size_t)maxc + k) * cap + src],
+                                              a.hin_d[(1 * (size_t)maxc + k) * cap + src],
+                                              a.hin_d[(2 * (size_t)maxc + k) * cap + src]);
+                                    break;
+                                }
+                            V3<T> Fc, Ftc, dnew;
+                            law_practical(L, n, delta, v, rw, Reff, meff, dold, Fc, Ftc, dnew);
+                            F = F + Fc;
+                            Tq = Tq + cross(n, Ftc) * ri;
+                            if (nnew < (uint32_t)maxc) {
+                                a.hout_pid[nnew * cap + q] = gid;
+                                a.hout_d[(0 * (size_t)maxc + nnew) * cap + q] = dnew.x;
+                                a.hout_d[(1 * (size_t)maxc + nnew) * cap + q] = dnew.y;
+                                a.hout_d[(2 * (size_t)maxc + nnew) * cap + q] = dnew.z;
+                            }
+                        } else {
+                            F = F + law_simple(L, n, delta, v);
+                            if (EVAL && nnew < (uint32_t)maxc) a.hout_pid[nnew * cap + q] = gid;
+                        }
+                        ++nnew;
+                        ++c_pp;
+                        c_maxov = fmaxf(c_maxov, (float)delta);
+                    }
+                }
+            }
+            // ---- walls (step 8)
+            for (int w = 0; w < S.nwalls; ++w) {
+                const WallDev& W = S.walls[w];
+                V3<T> n, cp;
+                T delta;
+                if (!PR::wall(W, me, S, n, delta, cp)) continue;
+                const V3<T> v = me.v - PR::wall_vel(W, cp);
+                const uint32_t gid = DEM_WALL_BASE + (uint32_t)w;
+                if (MODEL == 0) {
+                    const V3<T> rw = me.w * ri;
+                    V3<T> dold = mk(T(0), T(0), T(0));
+                    for (uint32_t k = 0; k < cnt_old; ++k)
+                        if (s_oid[k * bd + tid] == gid) {
+                            dold = mk(a.hin_d[(0 * (size_t)maxc + k) * cap + src],
+                                      a.hin_d[(1 * (size_t)maxc + k) * cap + src],
+                                      a.hin_d[(2 * (size_t)maxc + k) * cap + src]);
+                            break;
+                        }
+                    V3<T> Fc, Ftc, dnew;
+                    law_practical(L, n, delta, v, rw, ri, mi, dold, Fc, Ftc, dnew);
+                    F = F + Fc;
+                    Tq = Tq + cross(n, Ftc) * ri;
+                    if (nnew < (uint32_t)maxc) {
+                        a.hout_pid[nnew * cap + q] = gid;
+                        a.hout_d[(0 * (size_t)maxc + nnew) * cap + q] = dnew.x;
+                        a.hout_d[(1 * (size_t)maxc + nnew) * cap + q] = dnew.y;
+                        a.hout_d[(2 * (size_t)maxc + nnew) * cap + q] = dnew.z;
+                    }
+                } else {
+                    F = F + law_simple(L, n, delta, v);
+                    if (EVAL && nnew < (uint32_t)maxc) a.hout_pid[nnew * cap + q] = gid;
+                }
+                ++nnew;
+                ++c_wc;
+                c_maxov = fmaxf(c_maxov, (float)delta);
+            }
+            if (nnew > (uint32_t)maxc) raise_status(a.st, ST_CAPACITY, (int32_t)q);
+            c_nnew = nnew;
+            if (MODEL == 0 || EVAL) a.hout_cnt[q] = min(nnew, (uint32_t)maxc);
+            // gravity, once per particle
+            {
+                const T gx = sizeof(T) == 8 ? (T)S.g[0] : (T)S.g_f[0];
+                const T gy = sizeof(T) == 8 ? (T)S.g[1] : (T)S.g_f[1];
+                const T gz = sizeof(T) == 8 ? (T)S.g[2] : (T)S.g_f[2];
+                F = F + mk(gx, gy, gz) * mi;
+            }
+            if (EVAL) {
+                const size_t o = 3 * (size_t)me.id;
+                if (a.dbgF) { a.dbgF[o] = F.x; a.dbgF[o + 1] = F.y; a.dbgF[o + 2] = F.z; }
+                if (a.dbgT) { a.dbgT[o] = Tq.x; a.dbgT[o + 1] = Tq.y; a.dbgT[o + 2] = Tq.z; }
+            } else {
+                bool clamped = false, finite = true;
+                const uint32_t kk = PR::integrate(a.B, q, me, F, Tq, S, mi, clamped, finite);
+                if (!finite) raise_status(a.st, ST_NONFINITE, (int32_t)q);
+                c_clamp = clamped ? 1u : 0u;
+                a.key[q] = kk;
+                a.rank[q] = atomicAdd(&a.cnt[kk], 1u);
+            }
+        }
+    }
+    // warp-aggregated counters (every lane reaches this point)
+    const unsigned full = 0xffffffffu;
+    const uint32_t s_pp = __reduce_add_sync(full, c_pp);
+    const uint32_t s_wc = __reduce_add_sync(full, c_wc);
+    const uint32_t s_cl = __reduce_add_sync(full, c_clamp);
+    const uint32_t s_mx = __reduce_max_sync(full, c_nnew);
+    const uint32_t s_ov = __reduce_max_sync(full, __float_as_uint(c_maxov));
+    if ((tid & 31) == 0) {
+        if (s_pp) atomicAdd(&a.st->live.ncontacts, s_pp);
+        if (s_wc) atomicAdd(&a.st->live.nwallc, s_wc);
+        if (s_cl) atomicAdd(&a.st->live.clamped, s_cl);
+        if (s_mx) atomicMax(&a.st->live.max_nnew, s_mx);
+        if (s_ov) atomicMax(&a.st->live.max_overlap_bits, s_ov);
+    }
+}
+
+// ======================================================================= counting sort
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __restrict__ cnt, uint32_t m,
+                                                              uint32_t* __restrict__ part) {
+    __shared__ uint32_t ws[SCAN_THREADS / 32];
+    const uint32_t base = blockIdx.x * SCAN_TILE;
+    uint32_t s = 0;
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        const uint32_t k = base + i * SCAN_THREADS + threadIdx.x;
+        if (k < m) s += cnt[k];
+    }
+    s = __reduce_add_sync(0xffffffffu, s);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) t += ws[w];
+        part[blockIdx.x] = t;
+    }
+}
+
+// exclusive scan of part[0..nb) in one block of 1024 threads
+__global__ void __launch_bounds__(1024) k_scan_spine(uint32_t* part, uint32_t nb) {
+    __shared__ uint32_t sh[1024];
+    const uint32_t per = (nb + 1023) / 1024;
+    const uint32_t b0 = threadIdx.x * per;
+    uint32_t s = 0;
+    for (uint32_t k = 0; k < per; ++k)
+        if (b0 + k < nb) s += part[b0 + k];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+        const uint32_t v = threadIdx.x >= (uint32_t)off ? sh[threadIdx.x - off] : 0u;
+        __syncthreads();
+        sh[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = sh[threadIdx.x] - s;   // exclusive prefix of this thread's chunk
+    for (uint32_t k = 0; k < per; ++k)
+        if (b0 + k < nb) {
+            const uint32_t v = part[b0 + k];
+            part[b0 + k] = run;
+            run += v;
+        }
+}
+
+// cs[k] = exclusive prefix of cnt; cnt[k] = 0 for the next sort
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(uint32_t* __restrict__ cnt, uint32_t m,
+                                                            const uint32_t* __restrict__ part, uint32_t* __restrict__ cs) {
+    __shared__ uint32_t ws[SCAN_THREADS / 32];
+    const uint32_t base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+    uint32_t v[SCAN_ITEMS];
+    uint32_t s = 0;
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        const uint32_t k = base + i;
+        v[i] = k < m ? cnt[k] : 0u;
+        s += v[i];
+    }
+    // block-exclusive scan of the thread sums
+    const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    uint32_t inc = s;
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= (uint32_t)off) inc += t;
+    }
+    if (lane == 31) ws[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        uint32_t w = lane < SCAN_THREADS / 32 ? ws[lane] : 0u;
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= (uint32_t)off) w += t;
+        }
+        if (lane < SCAN_THREADS / 32) ws[lane] = w;
+    }
+    __syncthreads();
+    uint32_t run = part[blockIdx.x] + (inc - s) + (wid > 0 ? ws[wid - 1] : 0u);
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        const uint32_t k = base + i;
+        if (k < m) {
+            cs[k] = run;
+            cnt[k] = 0u;
+        }
+        run += v[i];
+    }
+}
+
+__global__ void k_scatter(uint32_t n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
+                          const uint32_t* __restrict__ cs, uint32_t* __restrict__ tmp) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < n) tmp[cs[key[q]] + rank[q]] = q;
+}
+
+// (cell, id) order: a particle's place in its cell is the number of cell-mates with a
+// smaller id. Gathers the state from B (pre-sort order) into A.
+template <class PR>
+__global__ void k_reorder(uint32_t n, typename PR::State A, typename PR::State B, const uint32_t* __restrict__ key,
+                          const uint32_t* __restrict__ cs, const uint32_t* __restrict__ tmp, uint32_t* __restrict__ perm,
+                          uint32_t* __restrict__ skey, StatusDev* st) {
+    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s == 0) {
+        st->last = st->live;
+        st->live = CountersDev{};
+    }
+    if (s >= n) return;
+    const uint32_t p = tmp[s];
+    const uint32_t c = key[p];
+    const uint32_t lo = cs[c], hi = cs[c + 1];
+    const uint32_t idp = B.id[p];
+    uint32_t r = 0;
+    for (uint32_t k = lo; k < hi; ++k) r += (B.id[tmp[k]] < idp) ? 1u : 0u;
+    const uint32_t q = lo + r;
+    PR::store(A, q, PR::load(B, p));
+    perm[q] = p;
+    skey[q] = c;
+}
+
+// ======================================================================= set-up / read-out
+template <class PR>
+__global__ void k_import(uint32_t n, typename PR::State B, const double* __restrict__ x, const double* __restrict__ v,
+                         const double* __restrict__ w, const float* __restrict__ r);
+
+template <>
+__global__ void k_import<PF64>(uint32_t n, StateF64 B, const double* __restrict__ x, const double* __restrict__ v,
+                               const double* __restrict__ w, const float* __restrict__ r) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    B.x[k] = x[3 * (size_t)k]; B.y[k] = x[3 * (size_t)k + 1]; B.z[k] = x[3 * (size_t)k + 2];
+    B.vx[k] = v[3 * (size_t)k]; B.vy[k] = v[3 * (size_t)k + 1]; B.vz[k] = v[3 * (size_t)k + 2];
+    B.wx[k] = w[3 * (size_t)k]; B.wy[k] = w[3 * (size_t)k + 1]; B.wz[k] = w[3 * (size_t)k + 2];
+    B.r[k] = r[k];
+    B.id[k] = k;
+}
+
+__device__ __forceinline__ void split_ff(double x, float& hi, float& lo) {
+    const float h = (float)x;
+    const float l = (float)(x - (double)h);
+    two_sum(h, l, hi, lo);
+}
+
+template <>
+__global__ void k_import<PF32>(uint32_t n, StateF32 B, const double* __restrict__ x, const double* __restrict__ v,
+                               const double* __restrict__ w, const float* __restrict__ r) {
+    const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    float h[3], l[3];
+    for (int a = 0; a < 3; ++a) split_ff(x[3 * (size_t)k + a], h[a], l[a]);
+    B.P0[k] = make_float4(h[0], h[1], h[2], r[k]);
+    B.P1[k] = make_float4(l[0], l[1], l[2], 0.f);
+    B.V[k] = make_float4((float)v[3 * (size_t)k], (float)v[3 * (size_t)k + 1], (float)v[3 * (size_t)k + 2], 0.f);
+    B.W[k] = make_float4((float)w[3 * (size_t)k], (float)w[3 * (size_t)k + 1], (float)w[3 * (size_t)k + 2], 0.f);
+    B.id[k] = k;
+}
+
+template <class PR>
+__global__ void k_hash_initial(uint32_t n, const SceneDev* scenes, int nscenes, typename PR::State B,
+                               uint32_t* __restrict__ key, uint32_t* __restrict__ rank, uint32_t* __restrict__ cnt,
+                               StatusDev* st) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const SceneDev& S = scenes[scene_of(scenes, nscenes, q)];
+    bool clamped = false;
+    const uint32_t kk = PR::key_of(B, S, q, clamped);
+    if (clamped) atomicAdd(&st->live.clamped, 1u);
+    key[q] = kk;
+    rank[q] = atomicAdd(&cnt[kk], 1u);
+}
+
+template <class PR>
+__global__ void k_export(uint32_t n, typename PR::State A, double* x, double* v, double* w);
+
+template <>
+__global__ void k_export<PF64>(uint32_t n, StateF64 A, double* x, double* v, double* w) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const size_t o = 3 * (size_t)A.id[q];
+    if (x) { x[o] = A.x[q]; x[o + 1] = A.y[q]; x[o + 2] = A.z[q]; }
+    if (v) { v[o] = A.vx[q]; v[o + 1] = A.vy[q]; v[o + 2] = A.vz[q]; }
+    if (w) { w[o] = A.wx[q]; w[o + 1] = A.wy[q]; w[o + 2] = A.wz[q]; }
+}
+
+template <>
+__global__ void k_export<PF32>(uint32_t n, StateF32 A, double* x, double* v, double* w) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const size_t o = 3 * (size_t)A.id[q];
+    if (x) {
+        const float4 h = A.P0[q], l = A.P1[q];
+        x[o] = (double)h.x + (double)l.x;
+        x[o + 1] = (double)h.y + (double)l.y;
+        x[o + 2] = (double)h.z + (double)l.z;
+    }
+    if (v) { const float4 a = A.V[q]; v[o] = a.x; v[o + 1] = a.y; v[o + 2] = a.z; }
+    if (w) { const float4 a = A.W[q]; w[o] = a.x; w[o + 1] = a.y; w[o + 2] = a.z; }
+}
+
+// ---------------------------------------------------------------- diagnostics (FP64)
+constexpr int DIAG_THREADS = 256;
+constexpr int NDIAG = 10;
+
+template <class PR>
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag(uint32_t n, const SceneDev* scenes, int nscenes,
+                                                       typename PR::State A, double* __restrict__ part) {
+    __shared__ double sh[NDIAG][DIAG_THREADS];
+    const uint32_t tid = threadIdx.x;
+    const uint32_t q = blockIdx.x * DIAG_THREADS + tid;
+    double val[NDIAG];
+    for (int k = 0; k < NDIAG; ++k) val[k] = 0.0;
+    if (q < n) {
+        const SceneDev& S = scenes[scene_of(scenes, nscenes, q)];
+        const typename PR::Self m = PR::load(A, q);
+        const V3<double> x = PR::pos(m), v = PR::vel(m), w = PR::spin(m);
+        const double r = (double)m.r;
+        const double mass = S.cmass * r * r * r;
+        const double I = 0.4 * mass * r * r;
+        val[0] = 0.5 * mass * dot(v, v);
+        val[1] = 0.5 * I * dot(w, w);
+        val[2] = mass * v.x; val[3] = mass * v.y; val[4] = mass * v.z;
+        const V3<double> L = cross(x, v) * mass + w * I;
+        val[5] = L.x; val[6] = L.y; val[7] = L.z;
+        val[8] = -mass * dot(mk(S.g[0], S.g[1], S.g[2]), x);
+        val[9] = mass;
+    }
+    for (int k = 0; k < NDIAG; ++k) sh[k][tid] = val[k];
+    __syncthreads();
+    for (uint32_t s = DIAG_THREADS / 2; s > 0; s >>= 1) {
+        if (tid < s)
+            for (int k = 0; k < NDIAG; ++k) sh[k][tid] += sh[k][tid + s];
+        __syncthreads();
+    }
+    if (tid == 0)
+        for (int k = 0; k < NDIAG; ++k) part[(size_t)blockIdx.x * NDIAG + k] = sh[k][0];
+}
+
+// one block: fixed-order reduction of the per-block partial sums
+__global__ void __launch_bounds__(DIAG_THREADS) k_diag_final(const double* __restrict__ part, uint32_t nb,
+                                                             double* __restrict__ out) {
+    __shared__ double sh[NDIAG][DIAG_THREADS];
+    const uint32_t tid = threadIdx.x;
+    double val[NDIAG];
+    for (int k = 0; k < NDIAG; ++k) val[k] = 0.0;
+    for (uint32_t b = tid; b < nb; b += DIAG_THREADS)
+        for (int k = 0; k < NDIAG; ++k) val[k] += part[(size_t)b * NDIAG + k];
+    for (int k = 0; k < NDIAG; ++k) sh[k][tid] = val[k];
+    __syncthreads();
+    for (uint32_t s = DIAG_THREADS / 2; s > 0; s >>= 1) {
+        if (tid < s)
+            for (int k = 0; k < NDIAG; ++k) sh[k][tid] += sh[k][tid + s];
+        __syncthreads();
+    }
+    if (tid == 0)
+        for (int k = 0; k < NDIAG; ++k) out[k] = sh[k][0];
+}
+
+// ======================================================================= launchers
+static inline uint32_t nblk(uint32_t n, uint32_t b) { return (n + b - 1) / b; }
+
+#define DEM_LAUNCH_CHECK()                          \
+    do {                                            \
+        ++d.launches;                               \
+        cudaError_t e_ = cudaGetLastError();        \
+        if (e_ != cudaSuccess) return e_;           \
+    } while (0)
+
+cudaError_t run_import(Domain& d, const double* x, const double* v, const double* w, const float* r) {
+    if (d.n == 0) return cudaSuccess;
+    if (d.precision == 0) k_import<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.B64, x, v, w, r);
+    else k_import<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.B32, x, v, w, r);
+    DEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+cudaError_t run_hash_initial(Domain& d) {
+    if (d.n == 0) return cudaSuccess;
+    if (d.precision == 0)
+        k_hash_initial<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.B64, d.key, d.rank,
+                                                                    d.cnt, d.st);
+    else
+        k_hash_initial<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.B32, d.key, d.rank,
+                                                                    d.cnt, d.st);
+    DEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+cudaError_t run_rebuild(Domain& d) {
+    if (d.n == 0) return cudaSuccess;
+    const uint32_t m = d.ncells + 1;
+    const uint32_t nb = nblk(m, SCAN_TILE);
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, d.stream>>>(d.cnt, m, d.part);
+    DEM_LAUNCH_CHECK();
+    k_scan_spine<<<1, 1024, 0, d.stream>>>(d.part, nb);
+    DEM_LAUNCH_CHECK();
+    k_scan_down<<<nb, SCAN_THREADS, 0, d.stream>>>(d.cnt, m, d.part, d.cs);
+    DEM_LAUNCH_CHECK();
+    k_scatter<<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.key, d.rank, d.cs, d.tmp);
+    DEM_LAUNCH_CHECK();
+    if (d.precision == 0)
+        k_reorder<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.A64, d.B64, d.key, d.cs, d.tmp, d.perm, d.skey, d.st);
+    else
+        k_reorder<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.A32, d.B32, d.key, d.cs, d.tmp, d.perm, d.skey, d.st);
+    DEM_LAUNCH_CHECK();
+    ++d.sorts;
+    return cudaSuccess;
+}
+
+template <class PR>
+static cudaError_t force_impl(Domain& d, const typename PR::State& A, const typename PR::State& B, bool eval,
+                              double* dbgF, double* dbgT) {
+    ForceArgs<PR> a;
+    a.scenes = d.d_scenes;
+    a.nscenes = d.nscenes;
+    a.n = d.n;
+    a.cap = d.cap;
+    a.maxc = d.maxc;
+    a.stiffness = d.stiffness;
+    a.A = A;
+    a.B = B;
+    a.skey = d.skey;
+    a.cs = d.cs;
+    a.perm = d.perm;
+    const int hi = d.h_cur, ho = 1 - d.h_cur;
+    a.hin_cnt = d.hcnt[hi];
+    a.hin_pid = d.hpid[hi];
+    a.hin_d = (const typename PR::T*)d.hd[hi];
+    a.hout_cnt = d.hcnt[ho];
+    a.hout_pid = d.hpid[ho];
+    a.hout_d = (typename PR::T*)d.hd[ho];
+    a.key = d.key;
+    a.rank = d.rank;
+    a.cnt = d.cnt;
+    a.st = d.st;
+    a.dbgF = dbgF;
+    a.dbgT = dbgT;
+    const uint32_t b = (uint32_t)d.block;
+    const size_t smem = (size_t)d.maxc * b * sizeof(uint32_t);
+    const uint32_t g = nblk(d.n, b);
+    if (d.model == 0) {
+        if (eval) k_force<PR, 0, true><<<g, b, smem, d.stream>>>(a);
+        else k_force<PR, 0, false><<<g, b, smem, d.stream>>>(a);
+    } else {
+        if (eval) k_force<PR, 1, true><<<g, b, smem, d.stream>>>(a);
+        else k_force<PR, 1, false><<<g, b, smem, d.stream>>>(a);
+    }
+    DEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+cudaError_t run_force(Domain& d, bool eval, double* dbgF, double* dbgT) {
+    if (d.n == 0) return cudaSuccess;
+    if (d.precision == 0) return force_impl<PF64>(d, d.A64, d.B64, eval, dbgF, dbgT);
+    return force_impl<PF32>(d, d.A32, d.B32, eval, dbgF, dbgT);
+}
+
+cudaError_t run_export(Domain& d, double* x, double* v, double* w) {
+    if (d.n == 0) return cudaSuccess;
+    if (d.precision == 0) k_export<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.A64, x, v, w);
+    else k_export<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.A32, x, v, w);
+    DEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+cudaError_t run_diag(Domain& d) {
+    const uint32_t nb = d.n ? nblk(d.n, DIAG_THREADS) : 1;
+    if (d.n) {
+        if (d.precision == 0)
+            k_diag<PF64><<<nb, DIAG_THREADS, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.A64, d.diag_part);
+        else
+            k_diag<PF32><<<nb, DIAG_THREADS, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.A32, d.diag_part);
+        DEM_LAUNCH_CHECK();
+        k_diag_final<<<1, DIAG_THREADS, 0, d.stream>>>(d.diag_part, nb, d.diag_out);
+        DEM_LAUNCH_CHECK();
+    } else {
+        cudaError_t e = cudaMemsetAsync(d.diag_out, 0, NDIAG * sizeof(double), d.stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace demgb

@@ -1,0 +1,350 @@
+"""Python binding of the C ABI in include/dem.h (libdemgb.so), same function names.
+
+Argument marshalling only: every step of the timestep runs in the CUDA library. Host
+arrays are numpy; device arrays are torch CUDA tensors (PyTorch supplies device memory
+and streams). If the library has not been built or cannot be loaded, `lib()` raises:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import _build
+
+DEM_OK = 0
+DEM_ERR = {1: "DEM_ERR_INVALID_ARG", 2: "DEM_ERR_OOM", 3: "DEM_ERR_CUDA", 4: "DEM_ERR_CAPACITY",
+           5: "DEM_ERR_TIMEOUT", 6: "DEM_ERR_NONFINITE", 7: "DEM_ERR_STATE"}
+DEM_PRACTICAL, DEM_SIMPLE = 0, 1
+DEM_LINEAR, DEM_HERTZ = 0, 1
+DEM_FP64, DEM_FP32 = 0, 1
+DEM_HOST, DEM_DEVICE = 0, 1
+DEM_PLANE, DEM_CYLINDER_IN = 0, 1
+WALL_BASE = 0xFFFFFF00
+
+_D3 = ctypes.c_double * 3
+
+
+class dem_config(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("stiffness", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("resort_interval", ctypes.c_int32), ("dt", ctypes.c_double), ("rho", ctypes.c_double),
+                ("g", _D3), ("kn", ctypes.c_double), ("kt", ctypes.c_double), ("cn", ctypes.c_double),
+                ("ct", ctypes.c_double), ("alpha", ctypes.c_double), ("mu", ctypes.c_double),
+                ("ksp", ctypes.c_double), ("kda", ctypes.c_double), ("ksh", ctypes.c_double),
+                ("skin", ctypes.c_double), ("cell_size", ctypes.c_double), ("domain_lo", _D3), ("domain_hi", _D3),
+                ("block_size", ctypes.c_int32), ("max_contacts", ctypes.c_int32)]
+
+
+class dem_wall(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pad", ctypes.c_int32), ("p", _D3), ("n", _D3), ("radius", ctypes.c_double),
+                ("omega", _D3), ("vel", _D3)]
+
+
+class DemError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{DEM_ERR.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+_EXPORTS = ["dem_create", "dem_set_particles", "dem_set_walls", "dem_step", "dem_get_state", "dem_get_forces",
+            "dem_get_history", "dem_restore", "dem_get_diagnostics", "dem_debug_snapshot", "dem_get_grid",
+            "dem_device_bytes", "dem_launch_count", "dem_last_error", "dem_destroy", "dem_set_timing",
+            "dem_get_phase_times"]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libdemgb.so (built by `paper_1301_1714_gb300._build.build()`)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first (python -c 'import __graft_entry__ as g; g.build()')")
+    L = ctypes.CDLL(path)
+    P, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    L.dem_create.argtypes = [ctypes.POINTER(dem_config), I32, P, ctypes.POINTER(P)]
+    L.dem_set_particles.argtypes = [P, I64, P, P, P, P, P, I32]
+    L.dem_set_walls.argtypes = [P, I32, P]
+    L.dem_step.argtypes = [P, I64]
+    L.dem_get_state.argtypes = [P, P, P, P, I32]
+    L.dem_get_forces.argtypes = [P, P, P, I32]
+    L.dem_get_history.argtypes = [P, I64, P, P, P, ctypes.POINTER(I64)]
+    L.dem_restore.argtypes = [P, I64, P, P, P, P, I64, P, P, P]
+    L.dem_get_diagnostics.argtypes = [P, P]
+    L.dem_debug_snapshot.argtypes = [P, P, P, I64, P, ctypes.POINTER(I64)]
+    L.dem_get_grid.argtypes = [P, P, P, P]
+    L.dem_set_timing.argtypes = [P, I32]
+    L.dem_get_phase_times.argtypes = [P, P]
+    L.dem_device_bytes.argtypes = [P]
+    L.dem_device_bytes.restype = I64
+    L.dem_launch_count.argtypes = [P]
+    L.dem_launch_count.restype = I64
+    L.dem_last_error.argtypes = [P]
+    L.dem_last_error.restype = ctypes.c_char_p
+    L.dem_destroy.argtypes = [P]
+    L.dem_destroy.restype = None
+    for name in _EXPORTS:
+        f = getattr(L, name)
+        if f.restype is ctypes.c_int or name in ("dem_create", "dem_set_particles", "dem_set_walls", "dem_step",
+                                                  "dem_get_state", "dem_get_forces", "dem_get_history", "dem_restore",
+                                                  "dem_get_diagnostics", "dem_debug_snapshot", "dem_get_grid",
+                                                  "dem_set_timing", "dem_get_phase_times"):
+            f.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(h, status):
+    if status != DEM_OK:
+        msg = lib().dem_last_error(h).decode() if h else ""
+        raise DemError(status, msg)
+
+
+# ------------------------------------------------------------------ marshalling
+def _host(a, dtype, shape):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if a.size != int(np.prod(shape)):
+        raise ValueError(f"expected {shape} elements of {dtype}, got {a.shape}")
+    return a
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def _is_device(a):
+    return a is not None and not isinstance(a, np.ndarray) and hasattr(a, "is_cuda") and a.is_cuda
+
+
+def config_from_params(p, block_size=0, max_contacts=0) -> dem_config:
+    """dem_config from a `scenes.Params`-like object."""
+    c = dem_config()
+    c.model = {"practical": DEM_PRACTICAL, "simple": DEM_SIMPLE}[p.model]
+    c.stiffness = {"linear": DEM_LINEAR, "hertz": DEM_HERTZ}[p.stiffness]
+    c.precision = {"fp64": DEM_FP64, "fp32": DEM_FP32}[p.precision]
+    c.resort_interval = int(getattr(p, "resort_interval", 1))
+    c.dt, c.rho = p.dt, p.rho
+    for a in range(3):
+        c.g[a] = p.g[a]
+        c.domain_lo[a] = p.domain_lo[a]
+        c.domain_hi[a] = p.domain_hi[a]
+    c.kn, c.kt, c.cn, c.ct, c.alpha, c.mu = p.kn, p.kt, p.cn, p.ct, p.alpha, p.mu
+    c.ksp, c.kda, c.ksh = p.ksp, p.kda, p.ksh
+    c.skin = getattr(p, "skin", 0.0)
+    c.cell_size = p.cell_size
+    c.block_size = block_size
+    c.max_contacts = max_contacts
+    return c
+
+
+def walls_array(walls):
+    arr = (dem_wall * max(1, len(walls)))()
+    for k, w in enumerate(walls):
+        arr[k].kind = {"plane": DEM_PLANE, "cylinder": DEM_CYLINDER_IN}[w["kind"]]
+        for a in range(3):
+            arr[k].p[a] = w["p"][a]
+            arr[k].n[a] = w["n"][a]
+            arr[k].omega[a] = w.get("omega", (0, 0, 0))[a]
+            arr[k].vel[a] = w.get("vel", (0, 0, 0))[a]
+        arr[k].radius = w.get("radius", 0.0)
+    return arr
+
+
+# ------------------------------------------------------------------ the C ABI, 1:1
+def dem_create(config, device=0, cuda_stream=None):
+    c = config if isinstance(config, dem_config) else config_from_params(config)
+    h = ctypes.c_void_p()
+    st = lib().dem_create(ctypes.byref(c), device, ctypes.c_void_p(cuda_stream) if cuda_stream else None,
+                          ctypes.byref(h))
+    if st != DEM_OK:
+        raise DemError(st, "dem_create rejected the configuration or device")
+    return h
+
+
+def dem_set_particles(h, x, v, w, r):
+    n = len(r)
+    if _is_device(r):
+        for t, dt in ((x, "torch.float64"), (v, "torch.float64"), (w, "torch.float64"), (r, "torch.float32")):
+            if not (_is_device(t) and str(t.dtype) == dt and t.is_contiguous()):
+                raise ValueError("device inputs must be contiguous CUDA tensors (x, v, w float64; r float32)")
+        _check(h, lib().dem_set_particles(h, n, None, _ptr(x), _ptr(v), _ptr(w), _ptr(r), DEM_DEVICE))
+        return
+    x = _host(x, np.float64, (n, 3)); v = _host(v, np.float64, (n, 3)); w = _host(w, np.float64, (n, 3))
+    r = _host(r, np.float32, (n,))
+    _check(h, lib().dem_set_particles(h, n, None, _ptr(x), _ptr(v), _ptr(w), _ptr(r), DEM_HOST))
+
+
+def dem_set_walls(h, walls):
+    arr = walls_array(walls)
+    _check(h, lib().dem_set_walls(h, len(walls), arr))
+
+
+def dem_step(h, nsteps=1):
+    _check(h, lib().dem_step(h, int(nsteps)))
+
+
+def dem_get_state(h, n, x=None, v=None, w=None):
+    """Host: returns (x, v, w) numpy (n, 3) arrays. Device: pass CUDA tensors to fill."""
+    if _is_device(x) or _is_device(v) or _is_device(w):
+        _check(h, lib().dem_get_state(h, _ptr(x), _ptr(v), _ptr(w), DEM_DEVICE))
+        return x, v, w
+    x = np.zeros((n, 3)); v = np.zeros((n, 3)); w = np.zeros((n, 3))
+    _check(h, lib().dem_get_state(h, _ptr(x), _ptr(v), _ptr(w), DEM_HOST))
+    return x, v, w
+
+
+def dem_get_forces(h, n, F=None, T=None):
+    if _is_device(F) or _is_device(T):
+        _check(h, lib().dem_get_forces(h, _ptr(F), _ptr(T), DEM_DEVICE))
+        return F, T
+    F = np.zeros((n, 3)); T = np.zeros((n, 3))
+    _check(h, lib().dem_get_forces(h, _ptr(F), _ptr(T), DEM_HOST))
+    return F, T
+
+
+HIST_DTYPE = np.dtype([("i", np.uint32), ("j", np.uint32), ("d", np.float64, (3,))])
+
+
+def dem_get_history(h):
+    """Stored tangential springs as a structured array (i, j, d[3]), sorted by (i, j)."""
+    cnt = ctypes.c_int64(0)
+    _check(h, lib().dem_get_history(h, 0, None, None, None, ctypes.byref(cnt)))
+    m = cnt.value
+    i = np.zeros(m, np.uint32); j = np.zeros(m, np.uint32); d = np.zeros((m, 3))
+    _check(h, lib().dem_get_history(h, m, _ptr(i), _ptr(j), _ptr(d), ctypes.byref(cnt)))
+    out = np.zeros(m, dtype=HIST_DTYPE)
+    out["i"], out["j"], out["d"] = i, j, d
+    return out
+
+
+def dem_restore(h, x, v, w, r, hist=None):
+    n = len(r)
+    x = _host(x, np.float64, (n, 3)); v = _host(v, np.float64, (n, 3)); w = _host(w, np.float64, (n, 3))
+    r = _host(r, np.float32, (n,))
+    if hist is None or len(hist) == 0:
+        _check(h, lib().dem_restore(h, n, _ptr(x), _ptr(v), _ptr(w), _ptr(r), 0, None, None, None))
+        return
+    i = np.ascontiguousarray(hist["i"], np.uint32); j = np.ascontiguousarray(hist["j"], np.uint32)
+    d = np.ascontiguousarray(hist["d"], np.float64)
+    _check(h, lib().dem_restore(h, n, _ptr(x), _ptr(v), _ptr(w), _ptr(r), len(i), _ptr(i), _ptr(j), _ptr(d)))
+
+
+DIAG_NAMES = ["ke_trans", "ke_rot", "px", "py", "pz", "lx", "ly", "lz", "pe_grav", "mass", "pair_contacts",
+              "wall_contacts", "max_overlap", "steps", "sorts", "clamped"]
+
+
+def dem_get_diagnostics(h):
+    out = np.zeros(16)
+    _check(h, lib().dem_get_diagnostics(h, _ptr(out)))
+    return out
+
+
+def dem_debug_snapshot(h, n, with_pairs=True):
+    """(cell per id, ids in (cell, id) order, pairs (m, 2) of the last dem_get_forces)."""
+    cell = np.zeros(n, np.uint32); order = np.zeros(n, np.uint32)
+    if not with_pairs:
+        _check(h, lib().dem_debug_snapshot(h, _ptr(cell), _ptr(order), 0, None, None))
+        return cell, order, None
+    cnt = ctypes.c_int64(0)
+    _check(h, lib().dem_debug_snapshot(h, None, None, 0, None, ctypes.byref(cnt)))
+    pairs = np.zeros((cnt.value, 2), np.uint32)
+    _check(h, lib().dem_debug_snapshot(h, _ptr(cell), _ptr(order), cnt.value, _ptr(pairs), ctypes.byref(cnt)))
+    return cell, order, pairs
+
+
+def dem_get_grid(h):
+    o = np.zeros(3); c = np.zeros(1); d = np.zeros(3, np.int64)
+    _check(h, lib().dem_get_grid(h, _ptr(o), _ptr(c), _ptr(d)))
+    return o, float(c[0]), tuple(int(k) for k in d)
+
+
+def dem_set_timing(h, enable=True):
+    _check(h, lib().dem_set_timing(h, 1 if enable else 0))
+
+
+def dem_get_phase_times(h):
+    """(force-pass ms, sort ms, force passes timed, sorts timed) since timing was enabled."""
+    out = np.zeros(4)
+    _check(h, lib().dem_get_phase_times(h, _ptr(out)))
+    return out
+
+
+def dem_device_bytes(h):
+    return int(lib().dem_device_bytes(h))
+
+
+def dem_launch_count(h):
+    return int(lib().dem_launch_count(h))
+
+
+def dem_last_error(h):
+    return lib().dem_last_error(h).decode()
+
+
+def dem_destroy(h):
+    if h:
+        lib().dem_destroy(h)
+
+
+# ------------------------------------------------------------------ convenience
+class Simulation:
+    """A handle plus its particle count (marshalling only)."""
+
+    def __init__(self, params, x, v, w, r, device=0, cuda_stream=None, block_size=0, max_contacts=0):
+        self.params = params
+        self.n = len(r)
+        self.h = dem_create(config_from_params(params, block_size, max_contacts), device, cuda_stream)
+        try:
+            dem_set_walls(self.h, params.walls)
+            dem_set_particles(self.h, x, v, w, r)
+        except Exception:
+            dem_destroy(self.h)
+            self.h = None
+            raise
+
+    def step(self, nsteps=1):
+        dem_step(self.h, nsteps)
+        return self
+
+    def state(self):
+        return dem_get_state(self.h, self.n)
+
+    def forces(self):
+        return dem_get_forces(self.h, self.n)
+
+    def history(self):
+        return dem_get_history(self.h)
+
+    def diagnostics(self):
+        return dict(zip(DIAG_NAMES, dem_get_diagnostics(self.h)))
+
+    def snapshot(self, with_pairs=True):
+        return dem_debug_snapshot(self.h, self.n, with_pairs)
+
+    def close(self):
+        if self.h:
+            dem_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -244,7 +244,7 @@ def box_lattice(seed: int = 1, nx: int = 16, ny: int = 16, nz: int = 8, r: float
     eta = alpha * math.sqrt(kn * meff)
     cn, ct = hertz_coeffs(kn, 2.0 / 7.0, r)
     p = Params(model=model, stiffness=stiffness, precision=precision, dt=dt, kn=kn, kt=kn * 2.0 / 7.0, cn=cn, ct=ct,
-               alpha=alpha, mu=mu, ksp=kn, kda=eta, ksh=eta, cell_size=auto_cell_size(r),
+               alpha=alpha, mu=mu, ksp=kn, kda=eta, ksh=eta, cell_size=auto_cell_size(float(rad.max())),
                domain_lo=lo, domain_hi=hi, walls=[_norm_wall(q) for q in box_walls(lo, hi)])
     return Scene(f"box_lattice_{n}_s{seed}", x, v, w, rad, p)
 
@@ -277,7 +277,7 @@ def box_rsa(seed: int = 1, n: int = 262_144, rbar: float = 1e-3, spread: float =
     eta = alpha * math.sqrt(kn * 0.5 * mbar)
     cn, ct = hertz_coeffs(kn, 2.0 / 7.0, rbar)
     p = Params(model=model, stiffness=stiffness, precision=precision, dt=dt, kn=kn, kt=kn * 2.0 / 7.0, cn=cn, ct=ct,
-               alpha=alpha, mu=mu, ksp=kn, kda=eta, ksh=eta, cell_size=auto_cell_size(rmax),
+               alpha=alpha, mu=mu, ksp=kn, kda=eta, ksh=eta, cell_size=auto_cell_size(float(rad.max())),
                domain_lo=lo, domain_hi=hi, walls=[_norm_wall(q) for q in box_walls(lo, hi)])
     return Scene(f"box_rsa_{n}_s{seed}", x, v, w, rad, p)
 
@@ -308,7 +308,7 @@ def drum(seed: int = 1, n: int = 4_194_304, rbar: float = 1e-3, spread: float = 
     lo = (0.0, -Rd, -Rd)
     hi = (L, Rd, Rd)
     p = Params(model=model, stiffness=stiffness, precision=precision, dt=dt, kn=kn, kt=kn * 2.0 / 7.0, cn=cn, ct=ct,
-               alpha=alpha, mu=mu, ksp=kn, kda=eta, ksh=eta, cell_size=auto_cell_size(rmax),
+               alpha=alpha, mu=mu, ksp=kn, kda=eta, ksh=eta, cell_size=auto_cell_size(float(rad.max())),
                domain_lo=lo, domain_hi=hi, walls=[_norm_wall(q) for q in drum_walls(Rd, L, omega)])
     return Scene(f"drum_{n}_s{seed}", x, v, w, rad, p)
 
