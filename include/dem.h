@@ -183,6 +183,31 @@ dem_status dem_get_grid(const dem_handle* h, double* origin, double* cell, int64
 dem_status dem_set_timing(dem_handle* h, int enable);
 dem_status dem_get_phase_times(const dem_handle* h, double* out4);
 
+/* Largest sizes dem_sort_cells_static accepts (its scratch is a fixed array). */
+#define DEM_STATIC_SORT_MAX_N 262144
+#define DEM_STATIC_SORT_MAX_CELLS 1048576
+
+/* Cell map and (cell, id) sort of n positions WITHOUT allocating device memory; the
+ * paper has no counterpart: it is for callers that cannot call cudaMalloc, such as a
+ * process that has already reserved all of the GPU's memory for its own pool, or a
+ * loop that forbids allocation after start-up because cudaMalloc/cudaFree can block or
+ * synchronise the device. The result is the one a handle computes in DEM_FP64 mode:
+ *   x          device, 3n doubles, particle k's position (id order)
+ *   origin, cell, dims   host: grid origin (3), cell edge, cells per axis (3)
+ *   cell_of    device out, n: cell key (k*ny + j)*nx + i of each particle (clamped)
+ *   order      device out, n: particle ids in (cell, id) order
+ *   cell_start device out, nx*ny*nz + 1: cell c holds order[cell_start[c] .. cell_start[c+1]-1]
+ *   cuda_stream  stream of the work (NULL = legacy default stream); the call returns
+ *              once the work is enqueued, on the calling thread's current device.
+ * The caller owns all buffers. Temporary storage is one fixed array of about 6 MB in the
+ * library's device memory, present on every GPU that loads the library until the
+ * process exits; n > DEM_STATIC_SORT_MAX_N or more than DEM_STATIC_SORT_MAX_CELLS cells
+ * returns DEM_ERR_INVALID_ARG. The first call on a device looks up that array's device
+ * address (once per device), so make the first call before any stream capture. All calls
+ * share the array: calls whose work overlaps on the GPU race and give wrong results. */
+dem_status dem_sort_cells_static(int64_t n, const double* x, const double* origin, double cell, const int64_t* dims,
+                                 uint32_t* cell_of, uint32_t* order, uint32_t* cell_start, void* cuda_stream);
+
 /* Bytes of device memory held by the handle. */
 int64_t dem_device_bytes(const dem_handle* h);
 

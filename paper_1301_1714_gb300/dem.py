@@ -52,7 +52,7 @@ _lib = None
 _EXPORTS = ["dem_create", "dem_set_particles", "dem_set_walls", "dem_step", "dem_get_state", "dem_get_forces",
             "dem_get_history", "dem_restore", "dem_get_diagnostics", "dem_debug_snapshot", "dem_get_grid",
             "dem_device_bytes", "dem_launch_count", "dem_last_error", "dem_destroy", "dem_set_timing",
-            "dem_get_phase_times"]
+            "dem_get_phase_times", "dem_sort_cells_static"]
 
 
 def lib_path() -> str:
@@ -80,6 +80,7 @@ def lib():
     L.dem_get_diagnostics.argtypes = [P, P]
     L.dem_debug_snapshot.argtypes = [P, P, P, I64, P, ctypes.POINTER(I64)]
     L.dem_get_grid.argtypes = [P, P, P, P]
+    L.dem_sort_cells_static.argtypes = [I64, P, P, ctypes.c_double, P, P, P, P, P]
     L.dem_set_timing.argtypes = [P, I32]
     L.dem_get_phase_times.argtypes = [P, P]
     L.dem_device_bytes.argtypes = [P]
@@ -95,7 +96,8 @@ def lib():
         if f.restype is ctypes.c_int or name in ("dem_create", "dem_set_particles", "dem_set_walls", "dem_step",
                                                   "dem_get_state", "dem_get_forces", "dem_get_history", "dem_restore",
                                                   "dem_get_diagnostics", "dem_debug_snapshot", "dem_get_grid",
-                                                  "dem_set_timing", "dem_get_phase_times"):
+                                                  "dem_set_timing", "dem_get_phase_times",
+                                                  "dem_sort_cells_static"):
             f.restype = ctypes.c_int
     _lib = L
     return L
@@ -267,6 +269,24 @@ def dem_get_grid(h):
     o = np.zeros(3); c = np.zeros(1); d = np.zeros(3, np.int64)
     _check(h, lib().dem_get_grid(h, _ptr(o), _ptr(c), _ptr(d)))
     return o, float(c[0]), tuple(int(k) for k in d)
+
+
+STATIC_SORT_MAX_N = 262144
+STATIC_SORT_MAX_CELLS = 1048576
+
+
+def dem_sort_cells_static(x, origin, cell, dims, cell_of, order, cell_start, cuda_stream=None):
+    """Cell map and (cell, id) sort without any device allocation by the library (for
+    callers that cannot allocate: see include/dem.h). x: CUDA float64 tensor (n, 3);
+    cell_of, order: CUDA int32 tensors (n,); cell_start: CUDA int32 tensor
+    (nx*ny*nz + 1,); the int32 buffers receive unsigned 32-bit values."""
+    n = int(x.shape[0]) if x is not None else 0
+    o = np.ascontiguousarray(origin, dtype=np.float64)
+    d = np.ascontiguousarray(dims, dtype=np.int64)
+    st = lib().dem_sort_cells_static(n, _ptr(x), _ptr(o), float(cell), _ptr(d), _ptr(cell_of), _ptr(order),
+                                     _ptr(cell_start), ctypes.c_void_p(cuda_stream) if cuda_stream else None)
+    if st != DEM_OK:
+        raise DemError(st, "dem_sort_cells_static: sizes above the static maximum, bad arguments or a CUDA error")
 
 
 def dem_set_timing(h, enable=True):
