@@ -48,12 +48,26 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["drum", "rsa", "box"], default="drum")
     ap.add_argument("--n", type=int, default=0, help="particle count (0 = the workload's own)")
-    ap.add_argument("--settle", type=int, default=2000)
+    ap.add_argument("--settle", type=int, default=3000,
+                    help="accelerated settling steps (input preparation, see settle_bed)")
+    ap.add_argument("--relax", type=int, default=1000, help="steps at the real parameters after settling")
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--resort", type=int, default=1,
+                    help="cell-sort interval: 1 = every step (Sec. 4.2); 0 = when a particle moved skin/2; "
+                         "K > 1 = at least every K steps (both with neighbour lists)")
+    ap.add_argument("--skin-r", type=float, default=0.1, help="skin in mean radii (used when --resort != 1)")
     ap.add_argument("--simple-steps", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--batch-scenes", type=int, default=256, help="scenes of the batched run (0 = skip)")
+    ap.add_argument("--batch-steps", type=int, default=300)
+    ap.add_argument("--batch-seq-scenes", type=int, default=32, help="scenes timed one by one for comparison")
+    ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving run (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-nmax", type=int, default=131072)
+    ap.add_argument("--serve-steps", type=str, default="500,2000", help="step budget range of the requests")
+    ap.add_argument("--serve-hbm-gb", type=float, default=16.0)
     return ap.parse_args()
 
 
@@ -71,11 +85,97 @@ def make_scene(args, rank=0):
 def workload_desc(args, sc):
     p = sc.params
     if args.workload == "drum":
+        sort = ("sort every step" if p.resort_interval == 1 else
+                f"sort when a particle moved skin/2 (skin {p.skin * 1e3:.2f} mm), neighbour lists")
         return (f"drum: {sc.n:,} spheres r~U[0.9,1.1] mm, drum R=300r L=208r rotating 2 rad/s, mu={p.mu}, e=0.7, "
-                f"practical linear kn={p.kn:g} N/m, dt={p.dt:.5e} s, FP32 forces + compensated positions, sort every step")
+                f"practical linear kn={p.kn:g} N/m, dt={p.dt:.5e} s, FP32 forces + compensated positions, {sort}")
     if args.workload == "rsa":
         return f"box settling: {sc.n:,} spheres r~U[0.8,1.2] mm, RSA loose fill, practical linear, FP32"
     return f"box: {sc.n:,} spheres r=1 mm, jittered lattice, practical linear, FP64"
+
+
+def settle_bed(dem, sc, dev_index, stream, steps, relax):
+    """Input preparation: the generated bed rests each sphere on one support only, so it is
+    settled before timing. `steps` steps run with dt x 8, g x 4 and e = 0.3 (fast, strongly
+    damped compaction; dt x 8 is still below the stability limit of the stiffest contact),
+    then the state is handed to the real parameters, which run `relax` further steps in
+    the caller's handle. Returns the settled (x, v, w)."""
+    from paper_1301_1714_gb300 import scenes
+    if steps <= 0:
+        return sc.x, sc.v, sc.w
+    p = sc.params
+    ps = p.copy(dt=8.0 * p.dt, g=tuple(4.0 * gk for gk in p.g), alpha=scenes.alpha_from_e(0.3), resort_interval=1,
+                skin=0.0, cell_size=scenes.auto_cell_size(float(sc.r.max())))
+    hs = dem.dem_create(dem.config_from_params(ps), dev_index, stream)
+    try:
+        dem.dem_set_walls(hs, ps.walls)
+        dem.dem_set_particles(hs, sc.x, sc.v, sc.w, sc.r)
+        dem.dem_step(hs, steps)
+        return dem.dem_get_state(hs, sc.n)
+    finally:
+        dem.dem_destroy(hs)
+
+
+def run_batch_bench(args, dem, dev_index, stream):
+    """256 independent box-settling scenes (log-uniform 1,024-65,536 spheres, mu ~
+    U[0.1, 0.6], e ~ U[0.5, 0.95]) advanced together in one batch, against the first
+    scenes advanced one by one through their own handles."""
+    import torch
+    from paper_1301_1714_gb300 import scenes
+    mix = scenes.batch_mix(seed=args.seed, count=args.batch_scenes, precision="fp32")
+    total = sum(sc.n for sc in mix)
+    b = dem.dem_batch_create(precision="fp32", device=dev_index, cuda_stream=stream.cuda_stream)
+    try:
+        for sc in mix:
+            dem.dem_batch_add(b, sc.params, sc.x, sc.v, sc.w, sc.r, args.batch_steps + 3)
+        dem.dem_batch_run(b, 3)                      # pack, first sort, graph capture
+        torch.cuda.synchronize()
+        l0 = dem.dem_batch_launch_count(b)
+        t0 = time.perf_counter()
+        dem.dem_batch_run(b, args.batch_steps)
+        tb = time.perf_counter() - t0
+        launches = dem.dem_batch_launch_count(b) - l0
+    finally:
+        dem.dem_batch_destroy(b)
+    seq_n, seq_t = 0, 0.0
+    for sc in mix[:args.batch_seq_scenes]:
+        h = dem.dem_create(dem.config_from_params(sc.params), dev_index, stream.cuda_stream)
+        try:
+            dem.dem_set_walls(h, sc.params.walls)
+            dem.dem_set_particles(h, sc.x, sc.v, sc.w, sc.r)
+            dem.dem_step(h, 3)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dem.dem_step(h, args.batch_steps)
+            seq_t += time.perf_counter() - t0
+            seq_n += sc.n
+        finally:
+            dem.dem_destroy(h)
+    batched = total * args.batch_steps / tb
+    seq = seq_n * args.batch_steps / seq_t if seq_t > 0 else None
+    return {"scenes": len(mix), "particles": total, "steps": args.batch_steps, "value": round(batched, 1),
+            "unit": UNIT, "ms_per_step": round(tb * 1e3 / args.batch_steps, 4), "gpu_launches": int(launches),
+            "sequential_value": round(seq, 1) if seq else None,
+            "sequential_sample": f"first {min(args.batch_seq_scenes, len(mix))} scenes, one handle each, "
+                                 f"{args.batch_steps} steps",
+            "batched_over_sequential": round(batched / seq, 2) if seq else None}
+
+
+def run_serve_bench(args, dem, dev_index, stream):
+    """Poisson request stream served by continuous batching; completion latency."""
+    from paper_1301_1714_gb300 import serve
+    smin, smax = (int(t) for t in args.serve_steps.split(","))
+    reqs = serve.poisson_requests(args.seed, args.serve_requests, args.serve_rate, 1024, args.serve_nmax, smin, smax)
+    offered = sum(r.scene.n * r.steps for r in reqs) / max(reqs[-1].arrival, 1e-9)
+    with serve.Server(int(args.serve_hbm_gb * 2 ** 30), cuda_stream=stream.cuda_stream, device=dev_index) as srv:
+        wall = srv.run(reqs)
+        stats = serve.latency_stats(srv.finished)
+        work = srv.particle_steps
+    return {"requests": len(reqs), "rate_per_s": args.serve_rate, "n_range": [1024, args.serve_nmax],
+            "step_range": [smin, smax], "hbm_budget_gb": args.serve_hbm_gb, "p50_s": round(stats["p50_s"], 3),
+            "p99_s": round(stats["p99_s"], 3), "value": round(work / wall, 1), "unit": UNIT,
+            "offered": round(offered, 1), "achieved_over_offered": round(work / wall / offered, 3),
+            "wall_s": round(wall, 2)}
 
 
 # ------------------------------------------------------------------ clocks
@@ -201,7 +301,7 @@ def oracle_sample(args, sc, target_s, max_steps=None):
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
-    from paper_1301_1714_gb300 import dem
+    from paper_1301_1714_gb300 import dem, replicas
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -216,21 +316,28 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
 
     sc = make_scene(args, rank)
+    if args.resort != 1:
+        skin = args.skin_r * 1e-3
+        sc.params = sc.params.copy(resort_interval=args.resort, skin=skin, cell_size=sc.params.cell_size + skin)
     p = sc.params
     N = sc.n
     cfg = dem.config_from_params(p)
+    t_prep = time.perf_counter()
+    xs0, vs0, ws0 = settle_bed(dem, sc, dev.index, stream.cuda_stream, args.settle, args.relax)
     h = dem.dem_create(cfg, dev.index, stream.cuda_stream)
     try:
         dem.dem_set_walls(h, p.walls)
-        dem.dem_set_particles(h, sc.x, sc.v, sc.w, sc.r)
-        if args.settle:
-            dem.dem_step(h, args.settle)
+        dem.dem_set_particles(h, xs0, vs0, ws0, sc.r)
+        if args.relax:
+            dem.dem_step(h, args.relax)
+        t_prep = time.perf_counter() - t_prep
         dem.dem_step(h, max(3, args.warmup))
         # ---------------- timed region (device events on the library's stream)
         if dist:
             dist.barrier()
         torch.cuda.synchronize(dev)
         dem.dem_set_timing(h, True)
+        sorts0 = dem.dem_get_diagnostics(h)[14]
         l0 = dem.dem_launch_count(h)
         clk = ClockSampler(physical_gpu_index(local_rank))
         clk.start()
@@ -245,18 +352,12 @@ def run_ours(args):
             dist.barrier()
         launches = dem.dem_launch_count(h) - l0
         ms = e0.elapsed_time(e1)
+        sorts_timed = dem.dem_get_diagnostics(h)[14] - sorts0
         phase = dem.dem_get_phase_times(h)
         dem.dem_set_timing(h, False)
         diag = dict(zip(dem.DIAG_NAMES, dem.dem_get_diagnostics(h)))
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
-            tot = torch.tensor([float(N)], device=dev, dtype=torch.float64)
-            dist.all_reduce(tot)
-            n_total = float(tot.item())
-        else:
-            n_total = float(N)
+        ms = replicas.reduce_max(ms, dev)            # the slowest replica sets the time
+        n_total = replicas.reduce_sum(float(N), dev)  # particles advanced by all replicas
         value = n_total * args.steps / (ms / 1e3)
 
         # ---------------- roofline of the dominant kernel (force pass)
@@ -321,11 +422,7 @@ def run_ours(args):
                 r_ = dem.lib().dem_get_state(he, dem._ptr(ox), dem._ptr(ov), dem._ptr(ow), dem.DEM_HOST)
                 if r_ != 0:
                     raise dem.DemError(r_, dem.dem_last_error(he))
-                te = time.perf_counter() - t0
-                if dist:
-                    t = torch.tensor([te], device=dev)
-                    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                    te = float(t.item())
+                te = replicas.reduce_max(time.perf_counter() - t0, dev)
             finally:
                 dem.dem_destroy(he)
             h2d = N * (3 * 24 + 4)
@@ -335,14 +432,19 @@ def run_ours(args):
                    "note": "one upload of the state, K steps, one download of the state (pinned host buffers), "
                            "through dem_set_particles / dem_step / dem_get_state"}
 
+        batch = run_batch_bench(args, dem, dev.index, stream) if args.batch_scenes > 0 else None
+        serving = run_serve_bench(args, dem, dev.index, stream) if args.serve_requests > 0 else None
         out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": workload_desc(args, sc), "n_particles": N, "seed": args.seed,
-                          "settle_steps": args.settle, "resort_interval": 1,
+                          "settle_steps": args.settle, "relax_steps": args.relax, "prep_s": round(t_prep, 1),
+                          "resort_interval": p.resort_interval, "skin_m": p.skin,
+                          "sorts_in_timed_steps": int(sorts_timed),
                           "l2": "inputs larger than L2 (no flush needed)",
                           "device_bytes": dem.dem_device_bytes(h), "parallelism": f"replicas x{world}"},
                "roofline": roof, "gpu_launches": int(launches), "clocks": clocks, "simple": simple, "e2e": e2e,
+               "batch": batch, "serving": serving,
                "diagnostics": {k: diag[k] for k in ("pair_contacts", "wall_contacts", "max_overlap", "ke_trans")}}
     finally:
         dem.dem_destroy(h)

@@ -72,15 +72,20 @@ enum { DEM_PLANE = 0, DEM_CYLINDER_IN = 1 };
  *  alpha       restitution parameter of Eq. 10: eta = alpha sqrt(k_n m_eff)
  *  mu          kinetic friction coefficient of Eq. 5
  *  ksp,kda,ksh spring, damping and shear coefficients of Eq. 1
- *  skin        Verlet skin [m]: with resort_interval != 1 the cell size grows by skin
- *              and the cell sort is skipped while every particle moved less than skin/2
+ *  skin        Verlet skin [m] (>= 0). The cell edge grows by skin.
  *  cell_size   grid cell edge [m]; 0 = 2 r_max (1 + 2^-10) + skin, r_max the largest
  *              radius passed to dem_set_particles. Must be >= that value.
  *  domain_lo/hi  box covered by the grid; particles outside use the nearest face cell.
- *  resort_interval 1 = sort every step (as in Sec. 4.2); 0 = automatic (skin-driven)
- *  block_size  threads per block of the force kernel; 0 = automatic (128)
+ *  resort_interval  1 = sort by cell every step and walk the 27 cells every step
+ *              (Sec. 4.2 as printed). 0 = sort (steps 2-4) only after some particle has
+ *              moved skin/2 since the last sort; at each sort a neighbour list of every
+ *              particle within r_i + r_j + skin is built from the 27 cells and the force
+ *              pass reads it instead of walking. K > 1 = as 0, and also at least every K
+ *              steps. 0 and K > 1 need skin > 0; they find exactly the same contacts.
+ *  block_size  threads per block of the force kernel (32..256); 0 = automatic (256)
  *  max_contacts  per-particle capacity of the contact/history list (incl. walls);
- *              0 = 32. Exceeding it makes dem_step return DEM_ERR_CAPACITY.
+ *              0 = 32; neighbour lists hold 2 x max_contacts. Exceeding either makes
+ *              dem_step return DEM_ERR_CAPACITY.
  */
 typedef struct {
     int32_t model;
@@ -182,6 +187,47 @@ dem_status dem_get_grid(const dem_handle* h, double* origin, double* cell, int64
  * [1] sort milliseconds, [2] force passes timed, [3] sorts timed. */
 dem_status dem_set_timing(dem_handle* h, int enable);
 dem_status dem_get_phase_times(const dem_handle* h, double* out4);
+
+/* ------------------------------------------------------------------------------ batches
+ * Many independent scenes advanced together: their particles are packed end to end in
+ * one domain and every kernel launch of a timestep (the force pass and the cell sort of
+ * Sec. 4.2) covers all of them; each particle reads its own scene's parameters, grid and
+ * walls. Scenes differ in size, dt, mu, alpha, walls and grid, but share precision,
+ * model and stiffness law. A scene's result does not depend on the other scenes in the
+ * batch. Scenes sort every step (resort_interval must be 1). */
+typedef struct dem_batch dem_batch;
+
+/* Creates an empty batch on `device` / `cuda_stream` (a non-legacy stream lets the step
+ * be replayed as a CUDA graph). max_contacts and block_size as in dem_config. */
+dem_status dem_batch_create(int precision, int model, int stiffness, int max_contacts, int block_size, int device,
+                            void* cuda_stream, dem_batch** out);
+
+/* Stages a scene (host arrays, id order, as dem_set_particles; walls as dem_set_walls)
+ * that enters the batch at the next dem_batch_run and advances step_budget steps of its
+ * own dt. *slot receives its identifier. */
+dem_status dem_batch_add(dem_batch* b, const dem_config* cfg, int nwalls, const dem_wall* walls, int64_t n,
+                         const double* x, const double* v, const double* w, const float* r, int64_t step_budget,
+                         int* slot);
+
+/* Advances the scenes that have steps left by up to max_steps steps, returning early
+ * when some scene reaches its budget; the slots that finished during this call are
+ * written to finished (at most cap; *nfinished receives the count). Scenes added or
+ * removed since the last call are packed in first (kept scenes keep state and springs). */
+dem_status dem_batch_run(dem_batch* b, int64_t max_steps, int* finished, int cap, int* nfinished);
+
+/* Current state of one scene, id order (any pointer may be NULL). */
+dem_status dem_batch_get_state(dem_batch* b, int slot, double* x, double* v, double* w, int where);
+
+/* Removes a scene (it leaves the domain at the next dem_batch_run). */
+dem_status dem_batch_remove(dem_batch* b, int slot);
+
+/* Particle count, steps done and step budget of a scene. */
+dem_status dem_batch_info(const dem_batch* b, int slot, int64_t* n, int64_t* steps_done, int64_t* budget);
+
+int64_t dem_batch_device_bytes(const dem_batch* b);
+int64_t dem_batch_launch_count(const dem_batch* b);
+const char* dem_batch_last_error(const dem_batch* b);
+void dem_batch_destroy(dem_batch* b);
 
 /* Largest sizes dem_sort_cells_static accepts (its scratch is a fixed array). */
 #define DEM_STATIC_SORT_MAX_N 262144

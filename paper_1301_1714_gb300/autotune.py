@@ -1,0 +1,61 @@
+"""Autotuner: picks the force kernel's block size and the sort policy (every step, or
+skin-driven with neighbour lists and a given skin, which also sets the cell size) for a
+scene by timing short runs of each candidate on the device.
+
+Every candidate finds exactly the same contacts, so the choice changes speed, not the
+physics (results differ only by the rounding of the per-particle sums).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import List, Optional, Sequence, Tuple
+
+from . import dem
+
+# (block size, resort_interval, skin as a fraction of the largest radius)
+DEFAULT_CANDIDATES: Tuple[Tuple[int, int, float], ...] = (
+    (256, 1, 0.0), (128, 1, 0.0),
+    (256, 0, 0.05), (256, 0, 0.1), (256, 0, 0.2), (128, 0, 0.1),
+)
+
+
+@dataclass
+class Choice:
+    block: int
+    resort: int
+    skin_frac: float
+    ms_per_step: float
+    force_ms: float
+    sort_ms: float
+
+
+def apply(params, rmax: float, choice: Choice):
+    """Parameters with the tuned sort policy (cell size = 2 r_max (1 + 2^-10) + skin)."""
+    from .scenes import auto_cell_size
+    skin = choice.skin_frac * rmax
+    return params.copy(resort_interval=choice.resort, skin=skin, cell_size=auto_cell_size(rmax, skin))
+
+
+def tune(params, x, v, w, r, candidates: Sequence[Tuple[int, int, float]] = DEFAULT_CANDIDATES, steps: int = 60,
+         warmup: int = 20, device: int = 0, cuda_stream=None) -> Tuple[Choice, List[Choice]]:
+    rmax = float(max(r)) if len(r) else 1.0
+    table: List[Choice] = []
+    for block, resort, sk in candidates:
+        c = Choice(block, resort, sk, 0.0, 0.0, 0.0)
+        p = apply(params, rmax, c)
+        h = dem.dem_create(dem.config_from_params(p, block_size=block), device, cuda_stream)
+        try:
+            dem.dem_set_walls(h, p.walls)
+            dem.dem_set_particles(h, x, v, w, r)
+            dem.dem_step(h, warmup)
+            dem.dem_set_timing(h, True)
+            dem.dem_step(h, steps)
+            ph = dem.dem_get_phase_times(h)
+        finally:
+            dem.dem_destroy(h)
+        c.force_ms = ph[0] / max(ph[2], 1)
+        c.sort_ms = ph[1] / max(ph[3], 1)
+        c.ms_per_step = c.force_ms + c.sort_ms
+        table.append(c)
+    best = min(table, key=lambda t: t.ms_per_step)
+    return best, table

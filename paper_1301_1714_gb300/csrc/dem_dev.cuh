@@ -63,6 +63,17 @@ struct StatusDev {
 
 enum : int32_t { ST_OK = 0, ST_CAPACITY = 4, ST_NONFINITE = 6 };
 
+// Step control, read and written only by kernels (the host never needs to know, while
+// stepping, whether a step sorted).
+struct CtrlDev {
+    int32_t cur;         // state set holding the current cell-sorted state (the other is "next")
+    int32_t rebuild;     // 1: this step ends with a cell sort (and, in list mode, new lists)
+    int32_t perm_valid;  // 1: the last step sorted, so stored springs are read through perm
+    int32_t since;       // steps since the last sort
+    uint32_t nsorts;     // sorts performed since the particles were set
+    int32_t pad[3];
+};
+
 __device__ __forceinline__ void raise_status(StatusDev* st, int32_t code, int32_t where) {
     if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
 }

@@ -36,9 +36,23 @@ struct Domain {
     SceneDev* d_scenes = nullptr;
     int scenes_cap = 0;
 
-    // particle state: A = cell-sorted current state, B = next state (pre-sort order)
-    StateF64 A64{}, B64{};
-    StateF32 A32{}, B32{};
+    // particle state: two sets; ctrl->cur (on the device) names the current, cell-sorted
+    // one, the other receives the next state
+    StateF64 S64[2]{};
+    StateF32 S32[2]{};
+    CtrlDev* ctrl = nullptr;       // device
+    CtrlDev* ctrl_host = nullptr;  // pinned copy
+
+    // neighbour lists (list mode: resort_interval != 1): candidates within r_i + r_j + skin
+    // of each particle at the last sort, slot-major nl[k*cap + q], counts ncnt[q]
+    int list_mode = 0;
+    int maxn = 64;
+    int interval = 1;              // sort at least every `interval` steps (0 = skin only)
+    float skin_f = 0.f;            // skin [m]
+    float thresh2 = 0.f;           // squared displacement that forces a sort
+    uint32_t* ncnt = nullptr;
+    uint32_t* nl = nullptr;
+    float4* ref = nullptr;         // positions at the last sort
 
     // tangential history, double-buffered; h_cur is the buffer the next step reads
     uint32_t* hcnt[2] = {nullptr, nullptr};
@@ -61,17 +75,35 @@ struct Domain {
     double* diag_out = nullptr;
 
     int64_t launches = 0;
-    int64_t sorts = 0;
 
     std::vector<void*> allocations;   // every cudaMalloc of this domain (freed together)
 };
 
+// A CUDA graph of two captured timesteps and the kernel launches it holds.
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches = 0;
+    void reset() {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        launches = 0;
+    }
+};
+
 // -------- launchers (dem_kernels.cu); all enqueue on d.stream and count launches
 cudaError_t run_import(Domain& d, const double* x, const double* v, const double* w, const float* r);
-cudaError_t run_hash_initial(Domain& d);
-cudaError_t run_rebuild(Domain& d);
+cudaError_t run_hash(Domain& d);      // cell key + in-cell rank of the next state (if sorting)
+cudaError_t run_rebuild(Domain& d);   // scan, scatter, (cell, id) gather, lists (if sorting)
+cudaError_t run_end_step(Domain& d);  // step bookkeeping (swap or keep, counters)
 cudaError_t run_force(Domain& d, bool eval, double* dbgF, double* dbgT);
 cudaError_t run_export(Domain& d, double* x, double* v, double* w);
 cudaError_t run_diag(Domain& d);   // fills d.diag_out[0..9] (device)
+// batches: springs into sorted order (into the free history buffer), new packed layout,
+// import of one scene at an offset, export of one scene's range
+cudaError_t run_hist_canon(Domain& d);
+cudaError_t run_repack(Domain& od, Domain& d, const uint32_t* map, uint32_t n_new);
+cudaError_t run_import_at(Domain& d, uint32_t p0, uint32_t np, const double* x, const double* v, const double* w,
+                          const float* r);
+cudaError_t run_export_range(Domain& d, uint32_t p0, uint32_t np, double* x, double* v, double* w);
 
 }  // namespace demgb

@@ -30,6 +30,7 @@ struct dem_handle {
     bool eval_valid = false;
     int64_t steps = 0;
     std::string err;
+    StepGraph graph;   // replayed by dem_step when timing is off and the stream is not the legacy one
     // phase timing (events around force passes and sorts)
     bool timing = false;
     std::vector<cudaEvent_t> events;
@@ -87,10 +88,10 @@ cudaError_t dmalloc(Domain& d, P** p, size_t bytes) {
 void free_particle_buffers(Domain& d) {
     for (void* p : d.allocations) cudaFree(p);
     d.allocations.clear();
-    d.A64 = StateF64{};
-    d.B64 = StateF64{};
-    d.A32 = StateF32{};
-    d.B32 = StateF32{};
+    d.S64[0] = d.S64[1] = StateF64{};
+    d.S32[0] = d.S32[1] = StateF32{};
+    d.ncnt = d.nl = nullptr;
+    d.ref = nullptr;
     for (int i = 0; i < 2; ++i) { d.hcnt[i] = nullptr; d.hpid[i] = nullptr; d.hd[i] = nullptr; }
     d.key = d.rank = d.tmp = d.perm = d.skey = d.cnt = d.cs = d.part = nullptr;
     d.diag_part = nullptr;
@@ -185,6 +186,10 @@ dem_status validate_config(const dem_config* c, std::string& why) {
             return DEM_ERR_INVALID_ARG;
         }
     if (c->resort_interval < 0) { why = "resort_interval"; return DEM_ERR_INVALID_ARG; }
+    if (c->resort_interval != 1 && !(c->skin > 0.0)) {
+        why = "resort_interval != 1 needs a skin > 0";
+        return DEM_ERR_INVALID_ARG;
+    }
     if (c->block_size != 0 && (c->block_size < 32 || c->block_size > 256 || c->block_size % 32)) {
         why = "block_size must be 0 or a multiple of 32 in [32, 256]";
         return DEM_ERR_INVALID_ARG;
@@ -194,8 +199,8 @@ dem_status validate_config(const dem_config* c, std::string& why) {
 }
 
 // (Re)allocate particle and cell buffers for n particles and ncells cells.
-dem_status ensure_buffers(dem_handle* h, uint32_t n, uint32_t ncells) {
-    Domain& d = h->d;
+// Device buffers of a domain for n particles and ncells cells (reused when large enough).
+dem_status alloc_domain(Domain& d, uint32_t n, uint32_t ncells, std::string& err) {
     const uint32_t need = std::max<uint32_t>(n, 1);
     if (need <= d.cap && ncells <= d.cells_cap) return DEM_OK;
     free_particle_buffers(d);
@@ -204,16 +209,16 @@ dem_status ensure_buffers(dem_handle* h, uint32_t n, uint32_t ncells) {
     const size_t N = cap;
     const size_t T = d.precision == 0 ? sizeof(double) : sizeof(float);
     cudaError_t e = cudaSuccess;
-#define AL(ptr, bytes) do { if ((e = dmalloc(d, &(ptr), (bytes))) != cudaSuccess) { free_particle_buffers(d); return fail(h, DEM_ERR_OOM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e)); } } while (0)
+#define AL(ptr, bytes) do { if ((e = dmalloc(d, &(ptr), (bytes))) != cudaSuccess) { free_particle_buffers(d); cudaGetLastError(); err = std::string("cudaMalloc failed: ") + cudaGetErrorString(e); return DEM_ERR_OOM; } } while (0)
     for (int s = 0; s < 2; ++s) {
         if (d.precision == 0) {
-            StateF64& S = s == 0 ? d.A64 : d.B64;
+            StateF64& S = d.S64[s];
             AL(S.x, N * 8); AL(S.y, N * 8); AL(S.z, N * 8);
             AL(S.vx, N * 8); AL(S.vy, N * 8); AL(S.vz, N * 8);
             AL(S.wx, N * 8); AL(S.wy, N * 8); AL(S.wz, N * 8);
             AL(S.r, N * 4); AL(S.id, N * 4);
         } else {
-            StateF32& S = s == 0 ? d.A32 : d.B32;
+            StateF32& S = d.S32[s];
             AL(S.P0, N * 16); AL(S.P1, N * 16); AL(S.V, N * 16); AL(S.W, N * 16); AL(S.id, N * 4);
         }
         AL(d.hcnt[s], N * 4);
@@ -221,6 +226,11 @@ dem_status ensure_buffers(dem_handle* h, uint32_t n, uint32_t ncells) {
         AL(d.hd[s], N * T * 3 * (size_t)d.maxc);
     }
     AL(d.key, N * 4); AL(d.rank, N * 4); AL(d.tmp, N * 4); AL(d.perm, N * 4); AL(d.skey, N * 4);
+    if (d.list_mode) {
+        AL(d.ncnt, N * 4);
+        AL(d.nl, N * 4 * (size_t)d.maxn);
+        AL(d.ref, N * 16);
+    }
     AL(d.cnt, ((size_t)ccap + 1) * 4);
     AL(d.cs, ((size_t)ccap + 1) * 4);
     const uint32_t nb = (ccap + 1 + 2047) / 2048;
@@ -233,8 +243,19 @@ dem_status ensure_buffers(dem_handle* h, uint32_t n, uint32_t ncells) {
     d.part_cap = nb;
     d.diag_part_cap = db;
     e = cudaMemsetAsync(d.cnt, 0, ((size_t)ccap + 1) * 4, d.stream);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemsetAsync(cnt)");
+    if (e != cudaSuccess) {
+        err = std::string("cudaMemsetAsync(cnt): ") + cudaGetErrorString(e);
+        return DEM_ERR_CUDA;
+    }
     return DEM_OK;
+}
+
+dem_status ensure_buffers(dem_handle* h, uint32_t n, uint32_t ncells) {
+    std::string err;
+    dem_status s = alloc_domain(h->d, n, ncells, err);
+    if (s == DEM_ERR_CUDA) h->broken = true;
+    if (s != DEM_OK) h->err = err;
+    return s;
 }
 
 dem_status ensure_stage(dem_handle* h, uint32_t n) {
@@ -274,6 +295,14 @@ dem_status sync_status(dem_handle* h) {
     return DEM_OK;
 }
 
+dem_status read_ctrl(dem_handle* h, CtrlDev& c) {
+    Domain& d = h->d;
+    CK(h, cudaMemcpyAsync(d.ctrl_host, d.ctrl, sizeof(CtrlDev), cudaMemcpyDeviceToHost, d.stream));
+    CK(h, cudaStreamSynchronize(d.stream));
+    c = *d.ctrl_host;
+    return DEM_OK;
+}
+
 dem_status rotate_counters(dem_handle* h) {
     Domain& d = h->d;
     CK(h, cudaMemcpyAsync(&d.st->last, &d.st->live, sizeof(CountersDev), cudaMemcpyDeviceToDevice, d.stream));
@@ -288,6 +317,7 @@ dem_status load_particles(dem_handle* h, int64_t n64, const double* x, const dou
     if (n64 < 0 || n64 > (int64_t)0x7FFFFF00) return fail(h, DEM_ERR_INVALID_ARG, "n out of range");
     const uint32_t n = (uint32_t)n64;
     if (where != DEM_HOST && where != DEM_DEVICE) return fail(h, DEM_ERR_INVALID_ARG, "where");
+    h->graph.reset();
     if (n > 0 && (!x || !v || !w || !r)) return fail(h, DEM_ERR_INVALID_ARG, "x, v, w and r are required");
     // radii (and, for host input, positions) are checked on the host
     std::vector<float> rh;
@@ -340,6 +370,17 @@ dem_status load_particles(dem_handle* h, int64_t n64, const double* x, const dou
     CK(h, cudaMemcpyAsync(d.d_scenes, d.h_scenes.data(), sizeof(SceneDev), cudaMemcpyHostToDevice, d.stream));
     CK(h, cudaMemsetAsync(d.st, 0, sizeof(StatusDev), d.stream));
     CK(h, cudaMemsetAsync(d.cnt, 0, ((size_t)d.ncells + 1) * 4, d.stream));
+    // step control: current set 0, the first step after the import sorts
+    *d.ctrl_host = CtrlDev{};
+    d.ctrl_host->rebuild = 1;
+    CK(h, cudaMemcpyAsync(d.ctrl, d.ctrl_host, sizeof(CtrlDev), cudaMemcpyHostToDevice, d.stream));
+    if (d.list_mode) {
+        // a particle that moved skin/2 less the FP32 position margin forces a sort
+        const double margin = (double)d.h_scenes[0].eps_f;
+        const double t = std::max(0.5 * c.skin - margin, 0.0);
+        d.thresh2 = (float)(t * t);
+        d.skin_f = (float)c.skin;
+    }
     d.h_cur = 0;
     if (n > 0) {
         CK(h, cudaMemsetAsync(d.hcnt[0], 0, (size_t)n * 4, d.stream));
@@ -356,13 +397,67 @@ dem_status load_particles(dem_handle* h, int64_t n64, const double* x, const dou
             xd = h->stage; vd = h->stage + 3 * (size_t)n; wd = h->stage + 6 * (size_t)n; rd = h->stage_r;
         }
         CK(h, run_import(d, xd, vd, wd, rd));
-        CK(h, run_hash_initial(d));
+        CK(h, run_hash(d));
         CK(h, run_rebuild(d));
+        CK(h, run_end_step(d));
     }
     h->has_particles = true;
     h->eval_valid = false;
     h->steps = 0;
     return DEM_OK;
+}
+
+
+// One timestep enqueued on d.stream: force pass, then (when this step sorts) hash, scan,
+// scatter, gather, lists, then the bookkeeping kernel.
+cudaError_t enqueue_step(Domain& d) {
+    cudaError_t e;
+    if ((e = run_force(d, false, nullptr, nullptr)) != cudaSuccess) return e;
+    d.h_cur = 1 - d.h_cur;
+    if (d.list_mode && (e = run_hash(d)) != cudaSuccess) return e;
+    if ((e = run_rebuild(d)) != cudaSuccess) return e;
+    return run_end_step(d);
+}
+
+// Two timesteps captured once as a CUDA graph (two, so that the history buffers return
+// to their starting roles) and replayed; plain launches on the legacy default stream.
+cudaError_t run_steps(Domain& d, StepGraph* g, int64_t nsteps) {
+    cudaError_t e;
+    if (!g || !d.stream || d.n == 0) {
+        for (int64_t k = 0; k < nsteps; ++k)
+            if ((e = enqueue_step(d)) != cudaSuccess) return e;
+        return cudaSuccess;
+    }
+    if (d.h_cur == 1 && nsteps > 0) {
+        if ((e = enqueue_step(d)) != cudaSuccess) return e;
+        --nsteps;
+    }
+    if (nsteps >= 2 && !g->exec) {
+        const int64_t l0 = d.launches;
+        if ((e = cudaStreamBeginCapture(d.stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+        cudaError_t e1 = enqueue_step(d);
+        cudaError_t e2 = e1 == cudaSuccess ? enqueue_step(d) : e1;
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(d.stream, &graph);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e);
+        }
+        g->launches = d.launches - l0;
+        d.launches = l0;
+        e = cudaGraphInstantiate(&g->exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            g->exec = nullptr;
+            return e;
+        }
+    }
+    for (; nsteps >= 2; nsteps -= 2) {
+        if ((e = cudaGraphLaunch(g->exec, d.stream)) != cudaSuccess) return e;
+        d.launches += g->launches;
+    }
+    if (nsteps == 1 && (e = enqueue_step(d)) != cudaSuccess) return e;
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -390,10 +485,16 @@ dem_status dem_create(const dem_config* cfg, int device, void* cuda_stream, dem_
     d.model = cfg->model;
     d.stiffness = cfg->stiffness;
     d.maxc = cfg->max_contacts > 0 ? cfg->max_contacts : 32;
-    d.block = cfg->block_size > 0 ? cfg->block_size : 128;
+    d.block = cfg->block_size > 0 ? cfg->block_size : 256;
+    d.list_mode = cfg->resort_interval != 1 ? 1 : 0;
+    d.interval = cfg->resort_interval;
+    d.maxn = 2 * d.maxc;
     d.stream = (cudaStream_t)cuda_stream;
     if (cudaMalloc(&d.st, sizeof(StatusDev)) != cudaSuccess ||
         cudaMallocHost(&d.st_host, sizeof(StatusDev)) != cudaSuccess ||
+        cudaMalloc(&d.ctrl, sizeof(CtrlDev)) != cudaSuccess ||
+        cudaMallocHost(&d.ctrl_host, sizeof(CtrlDev)) != cudaSuccess ||
+        cudaMemset(d.ctrl, 0, sizeof(CtrlDev)) != cudaSuccess ||
         cudaMalloc(&d.diag_out, 16 * sizeof(double)) != cudaSuccess ||
         cudaMemset(d.st, 0, sizeof(StatusDev)) != cudaSuccess) {
         cudaGetLastError();
@@ -466,13 +567,19 @@ dem_status dem_step(dem_handle* h, int64_t nsteps) {
             h->events.push_back(e);
         }
     }
-    for (int64_t s = 0; s < nsteps; ++s) {
-        if (timed) CK(h, cudaEventRecord(h->events[3 * s], d.stream));
-        CK(h, run_force(d, false, nullptr, nullptr));
-        if (timed) CK(h, cudaEventRecord(h->events[3 * s + 1], d.stream));
-        d.h_cur = 1 - d.h_cur;
-        CK(h, run_rebuild(d));
-        if (timed) CK(h, cudaEventRecord(h->events[3 * s + 2], d.stream));
+    if (timed) {
+        for (int64_t s = 0; s < nsteps; ++s) {
+            CK(h, cudaEventRecord(h->events[3 * s], d.stream));
+            CK(h, run_force(d, false, nullptr, nullptr));
+            CK(h, cudaEventRecord(h->events[3 * s + 1], d.stream));
+            d.h_cur = 1 - d.h_cur;
+            if (d.list_mode) CK(h, run_hash(d));   // (sort steps only; fused into the force pass otherwise)
+            CK(h, run_rebuild(d));
+            CK(h, run_end_step(d));
+            CK(h, cudaEventRecord(h->events[3 * s + 2], d.stream));
+        }
+    } else {
+        CK(h, run_steps(d, &h->graph, nsteps));
     }
     h->steps += nsteps;
     if (nsteps > 0) h->eval_valid = false;
@@ -578,10 +685,14 @@ dem_status dem_get_history(dem_handle* h, int64_t cap, uint32_t* oi, uint32_t* o
     if (n == 0 || d.model != 0) return DEM_OK;
     std::vector<uint32_t> perm, ids, cnt;
     dem_status s;
+    CtrlDev ctl;
+    if ((s = read_ctrl(h, ctl)) != DEM_OK) return s;
     if ((s = download_u32(h, perm, d.perm, n)) != DEM_OK) return s;
-    if ((s = download_u32(h, ids, d.precision == 0 ? d.A64.id : d.A32.id, n)) != DEM_OK) return s;
+    if ((s = download_u32(h, ids, d.precision == 0 ? d.S64[ctl.cur].id : d.S32[ctl.cur].id, n)) != DEM_OK) return s;
     if ((s = download_u32(h, cnt, d.hcnt[d.h_cur], N)) != DEM_OK) return s;
     CK(h, cudaStreamSynchronize(d.stream));
+    if (!ctl.perm_valid)
+        for (size_t q = 0; q < n; ++q) perm[q] = (uint32_t)q;
     uint32_t mx = 0;
     for (size_t q = 0; q < n; ++q) mx = std::max(mx, std::min<uint32_t>(cnt[perm[q]], (uint32_t)M));
     std::vector<uint32_t> pid((size_t)mx * N);
@@ -686,6 +797,7 @@ dem_status dem_get_diagnostics(dem_handle* h, double* out) {
     double tmp[10];
     CK(h, cudaMemcpyAsync(tmp, d.diag_out, 10 * sizeof(double), cudaMemcpyDeviceToHost, d.stream));
     CK(h, cudaMemcpyAsync(d.st_host, d.st, sizeof(StatusDev), cudaMemcpyDeviceToHost, d.stream));
+    CK(h, cudaMemcpyAsync(d.ctrl_host, d.ctrl, sizeof(CtrlDev), cudaMemcpyDeviceToHost, d.stream));
     CK(h, cudaStreamSynchronize(d.stream));
     for (int k = 0; k < 10; ++k) out[k] = tmp[k];
     const CountersDev& c = d.st_host->last;
@@ -695,7 +807,7 @@ dem_status dem_get_diagnostics(dem_handle* h, double* out) {
     out[11] = (double)c.nwallc;
     out[12] = (double)mo;
     out[13] = (double)h->steps;
-    out[14] = (double)d.sorts;
+    out[14] = (double)d.ctrl_host->nsorts;
     out[15] = (double)c.clamped;
     return DEM_OK;
 }
@@ -710,7 +822,9 @@ dem_status dem_debug_snapshot(dem_handle* h, uint32_t* cell, uint32_t* order, in
     const size_t n = d.n, N = d.cap;
     std::vector<uint32_t> ids, skey;
     dem_status s;
-    if ((s = download_u32(h, ids, d.precision == 0 ? d.A64.id : d.A32.id, n)) != DEM_OK) return s;
+    CtrlDev ctl;
+    if ((s = read_ctrl(h, ctl)) != DEM_OK) return s;
+    if ((s = download_u32(h, ids, d.precision == 0 ? d.S64[ctl.cur].id : d.S32[ctl.cur].id, n)) != DEM_OK) return s;
     if ((s = download_u32(h, skey, d.skey, n)) != DEM_OK) return s;
     CK(h, cudaStreamSynchronize(d.stream));
     if (cell)
@@ -769,6 +883,7 @@ int64_t dem_device_bytes(const dem_handle* h) {
     size_t b = 2 * state + 2 * (N * 4 + N * 4 * M + N * T * 3 * M) + 5 * N * 4 + 2 * C * 4 + (size_t)d.part_cap * 4 +
                (size_t)d.diag_part_cap * 80 + sizeof(StatusDev) + 128 + sizeof(SceneDev) * d.scenes_cap;
     b += (size_t)h->stage_cap * (9 * 8 + 4);
+    if (d.list_mode) b += N * (4 + 4 * (size_t)d.maxn + 16);
     return (int64_t)b;
 }
 
@@ -785,12 +900,481 @@ void dem_destroy(dem_handle* h) {
     if (h->d.d_scenes) cudaFree(h->d.d_scenes);
     if (h->d.st) cudaFree(h->d.st);
     if (h->d.st_host) cudaFreeHost(h->d.st_host);
+    if (h->d.ctrl) cudaFree(h->d.ctrl);
+    if (h->d.ctrl_host) cudaFreeHost(h->d.ctrl_host);
     if (h->d.diag_out) cudaFree(h->d.diag_out);
     if (h->stage) cudaFree(h->stage);
     if (h->stage_r) cudaFree(h->stage_r);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    h->graph.reset();
     cudaGetLastError();
     delete h;
+}
+
+}  // extern "C"
+
+// =========================================================================== batches
+// Many independent scenes packed end to end in one domain: every kernel launch of a step
+// covers all of them (each particle finds its scene's parameters, grid and walls in the
+// scene table), so uneven scenes advance together in one launch sequence, replayed as a
+// CUDA graph. Scenes are added as arrays and enter at the next dem_batch_run, when the
+// domain is repacked (kept scenes keep their state and springs, finished or removed
+// scenes leave). Each scene advances until its own step budget; then it is frozen
+// (carried unchanged) until it is removed.
+namespace {
+
+struct BatchScene {
+    int slot = -1;
+    dem_config cfg{};
+    std::vector<dem_wall> walls;
+    int64_t n = 0, budget = 0, done = 0;
+    bool in_domain = false, removed = false;
+    std::vector<double> x, v, w;   // staged input until the scene enters the domain
+    std::vector<float> r;
+    double rmax = 0.0, origin[3] = {0, 0, 0}, h = 0.0;
+    int64_t dims[3] = {1, 1, 1};
+    uint32_t p0 = 0, c0 = 0, ncell = 1;
+};
+
+}  // namespace
+
+struct dem_batch {
+    Domain d;
+    int device = 0;
+    std::vector<BatchScene> scenes;
+    int next_slot = 0;
+    bool dirty = false;
+    bool broken = false;
+    std::string err;
+    StepGraph graph;
+    double* stage = nullptr;
+    float* stage_r = nullptr;
+    size_t stage_cap = 0;
+    uint32_t* d_map = nullptr;
+    size_t map_cap = 0;
+};
+
+namespace {
+
+dem_status bfail(dem_batch* b, dem_status s, const std::string& m) {
+    if (b) b->err = m;
+    return s;
+}
+dem_status bcuda(dem_batch* b, cudaError_t e, const char* what) {
+    if (b) {
+        b->broken = true;
+        b->err = std::string(what) + ": " + cudaGetErrorString(e);
+    }
+    return DEM_ERR_CUDA;
+}
+#define BCK(b, expr)                                                   \
+    do {                                                               \
+        cudaError_t e__ = (expr);                                      \
+        if (e__ != cudaSuccess) return bcuda((b), e__, #expr);         \
+    } while (0)
+
+// Scene table entry of a batch scene (the same fields a handle fills for its one scene).
+void fill_batch_scene(const BatchScene& sc, SceneDev& S) {
+    dem_handle tmp;
+    tmp.cfg = sc.cfg;
+    tmp.walls = sc.walls;
+    tmp.rmax = sc.rmax;
+    tmp.h = sc.h;
+    for (int a = 0; a < 3; ++a) {
+        tmp.origin[a] = sc.origin[a];
+        tmp.dims[a] = sc.dims[a];
+    }
+    fill_scene(&tmp, S, sc.p0, (uint32_t)sc.n, sc.c0);
+}
+
+// Rebuild the packed domain: kept scenes (state + springs), then the staged ones.
+dem_status repack(dem_batch* b) {
+    Domain& od = b->d;
+    std::vector<BatchScene*> kept, fresh;
+    for (auto& sc : b->scenes) {
+        if (sc.removed) continue;
+        (sc.in_domain ? kept : fresh).push_back(&sc);
+    }
+    // new layout
+    uint64_t n_new = 0, c_new = 0;
+    std::vector<uint32_t> map;
+    for (BatchScene* sc : kept) {
+        for (int64_t k = 0; k < sc->n; ++k) map.push_back(sc->p0 + (uint32_t)k);
+    }
+    uint32_t p = 0, c = 0;
+    for (BatchScene* sc : kept) {
+        sc->p0 = p;
+        sc->c0 = c;
+        p += (uint32_t)sc->n;
+        c += sc->ncell;
+    }
+    for (BatchScene* sc : fresh) {
+        sc->p0 = p;
+        sc->c0 = c;
+        p += (uint32_t)sc->n;
+        c += sc->ncell;
+        for (int64_t k = 0; k < sc->n; ++k) map.push_back(0xFFFFFFFFu);
+    }
+    n_new = p;
+    c_new = c;
+    if (n_new > 0x7FFFFF00ull || c_new > 0x7FFFFFFFull) return bfail(b, DEM_ERR_INVALID_ARG, "batch too large");
+    // springs of the current state into sorted order (old domain), then the new domain
+    if (od.n > 0) BCK(b, run_hist_canon(od));
+    Domain nd;
+    nd.precision = od.precision;
+    nd.model = od.model;
+    nd.stiffness = od.stiffness;
+    nd.maxc = od.maxc;
+    nd.maxn = od.maxn;
+    nd.block = od.block;
+    nd.stream = od.stream;
+    nd.list_mode = 0;
+    nd.interval = 1;
+    nd.st = od.st;
+    nd.st_host = od.st_host;
+    nd.ctrl = od.ctrl;
+    nd.ctrl_host = od.ctrl_host;
+    nd.diag_out = od.diag_out;
+    nd.launches = od.launches;
+    nd.n = (uint32_t)n_new;
+    nd.ncells = (uint32_t)std::max<uint64_t>(c_new, 1);
+    std::string err;
+    dem_status s = alloc_domain(nd, nd.n, nd.ncells, err);
+    if (s != DEM_OK) return bfail(b, s, err);
+    // scene table
+    const int ns = (int)(kept.size() + fresh.size());
+    nd.nscenes = ns;
+    nd.h_scenes.assign(std::max(ns, 1), SceneDev{});
+    int k = 0;
+    for (BatchScene* sc : kept) fill_batch_scene(*sc, nd.h_scenes[k++]);
+    for (BatchScene* sc : fresh) fill_batch_scene(*sc, nd.h_scenes[k++]);
+    for (k = 0; k < ns; ++k) {
+        BatchScene* sc = k < (int)kept.size() ? kept[k] : fresh[k - kept.size()];
+        nd.h_scenes[k].active = sc->done < sc->budget ? 1 : 0;
+    }
+    if (cudaMalloc(&nd.d_scenes, sizeof(SceneDev) * std::max(ns, 1)) != cudaSuccess) {
+        cudaGetLastError();
+        free_particle_buffers(nd);
+        return bfail(b, DEM_ERR_OOM, "cudaMalloc(scene table) failed");
+    }
+    nd.scenes_cap = std::max(ns, 1);
+    BCK(b, cudaMemcpyAsync(nd.d_scenes, nd.h_scenes.data(), sizeof(SceneDev) * ns, cudaMemcpyHostToDevice, nd.stream));
+    // old -> new particle map, kept springs and state
+    if (n_new > 0) {
+        if (b->map_cap < n_new) {
+            if (b->d_map) cudaFree(b->d_map);
+            b->d_map = nullptr;
+            if (cudaMalloc(&b->d_map, n_new * 4) != cudaSuccess) {
+                cudaGetLastError();
+                return bfail(b, DEM_ERR_OOM, "cudaMalloc(map) failed");
+            }
+            b->map_cap = n_new;
+        }
+        BCK(b, cudaMemcpyAsync(b->d_map, map.data(), n_new * 4, cudaMemcpyHostToDevice, nd.stream));
+        BCK(b, run_repack(od, nd, b->d_map, (uint32_t)n_new));
+    }
+    // staged scenes
+    for (BatchScene* sc : fresh) {
+        const size_t n = (size_t)sc->n;
+        if (n == 0) continue;
+        if (b->stage_cap < n) {
+            if (b->stage) cudaFree(b->stage);
+            if (b->stage_r) cudaFree(b->stage_r);
+            b->stage = nullptr;
+            b->stage_r = nullptr;
+            if (cudaMalloc(&b->stage, n * 72) != cudaSuccess || cudaMalloc(&b->stage_r, n * 4) != cudaSuccess) {
+                cudaGetLastError();
+                return bfail(b, DEM_ERR_OOM, "cudaMalloc(stage) failed");
+            }
+            b->stage_cap = n;
+        }
+        BCK(b, cudaMemcpyAsync(b->stage, sc->x.data(), n * 24, cudaMemcpyHostToDevice, nd.stream));
+        BCK(b, cudaMemcpyAsync(b->stage + 3 * n, sc->v.data(), n * 24, cudaMemcpyHostToDevice, nd.stream));
+        BCK(b, cudaMemcpyAsync(b->stage + 6 * n, sc->w.data(), n * 24, cudaMemcpyHostToDevice, nd.stream));
+        BCK(b, cudaMemcpyAsync(b->stage_r, sc->r.data(), n * 4, cudaMemcpyHostToDevice, nd.stream));
+        BCK(b, run_import_at(nd, sc->p0, (uint32_t)n, b->stage, b->stage + 3 * n, b->stage + 6 * n, b->stage_r));
+        BCK(b, cudaStreamSynchronize(nd.stream));   // the stage is reused by the next scene
+        sc->in_domain = true;
+        std::vector<double>().swap(sc->x);
+        std::vector<double>().swap(sc->v);
+        std::vector<double>().swap(sc->w);
+        std::vector<float>().swap(sc->r);
+    }
+    // first sort of the new layout
+    *nd.ctrl_host = CtrlDev{};
+    nd.ctrl_host->rebuild = 1;
+    BCK(b, cudaStreamSynchronize(nd.stream));
+    BCK(b, cudaMemcpyAsync(nd.ctrl, nd.ctrl_host, sizeof(CtrlDev), cudaMemcpyHostToDevice, nd.stream));
+    BCK(b, cudaMemsetAsync(nd.cnt, 0, ((size_t)nd.ncells + 1) * 4, nd.stream));
+    nd.h_cur = 0;
+    BCK(b, run_hash(nd));
+    BCK(b, run_rebuild(nd));
+    BCK(b, run_end_step(nd));
+    BCK(b, cudaStreamSynchronize(nd.stream));
+    // swap in
+    b->graph.reset();
+    free_particle_buffers(od);
+    if (od.d_scenes) cudaFree(od.d_scenes);
+    od.d_scenes = nullptr;
+    Domain keep_shared = od;   // status, ctrl and diag buffers are shared
+    (void)keep_shared;
+    b->d = nd;
+    // drop removed scenes from the list
+    std::vector<BatchScene> left;
+    for (auto& sc : b->scenes)
+        if (!sc.removed) left.push_back(std::move(sc));
+    b->scenes = std::move(left);
+    b->dirty = false;
+    return DEM_OK;
+}
+
+BatchScene* find_slot(dem_batch* b, int slot) {
+    for (auto& sc : b->scenes)
+        if (sc.slot == slot && !sc.removed) return &sc;
+    return nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+dem_status dem_batch_create(int precision, int model, int stiffness, int max_contacts, int block_size, int device,
+                            void* cuda_stream, dem_batch** out) {
+    if (!out) return DEM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if ((precision != DEM_FP64 && precision != DEM_FP32) || (model != DEM_PRACTICAL && model != DEM_SIMPLE) ||
+        (stiffness != DEM_LINEAR && stiffness != DEM_HERTZ) || max_contacts < 0 || max_contacts > 64 ||
+        (block_size != 0 && (block_size < 32 || block_size > 256 || block_size % 32)))
+        return DEM_ERR_INVALID_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return DEM_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(device);
+    dem_batch* b = new dem_batch();
+    b->device = device;
+    Domain& d = b->d;
+    d.precision = precision;
+    d.model = model;
+    d.stiffness = stiffness;
+    d.maxc = max_contacts > 0 ? max_contacts : 32;
+    d.maxn = 2 * d.maxc;
+    d.block = block_size > 0 ? block_size : 256;
+    d.stream = (cudaStream_t)cuda_stream;
+    if (cudaMalloc(&d.st, sizeof(StatusDev)) != cudaSuccess || cudaMallocHost(&d.st_host, sizeof(StatusDev)) != cudaSuccess ||
+        cudaMalloc(&d.ctrl, sizeof(CtrlDev)) != cudaSuccess || cudaMallocHost(&d.ctrl_host, sizeof(CtrlDev)) != cudaSuccess ||
+        cudaMalloc(&d.diag_out, 16 * sizeof(double)) != cudaSuccess || cudaMemset(d.st, 0, sizeof(StatusDev)) != cudaSuccess ||
+        cudaMemset(d.ctrl, 0, sizeof(CtrlDev)) != cudaSuccess) {
+        cudaGetLastError();
+        dem_batch_destroy(b);
+        return DEM_ERR_OOM;
+    }
+    *out = b;
+    return DEM_OK;
+}
+
+dem_status dem_batch_add(dem_batch* b, const dem_config* cfg, int nwalls, const dem_wall* walls, int64_t n,
+                         const double* x, const double* v, const double* w, const float* r, int64_t step_budget,
+                         int* slot) {
+    if (!b || !slot) return DEM_ERR_INVALID_ARG;
+    if (b->broken) return bfail(b, DEM_ERR_STATE, "batch is unusable after a CUDA error");
+    std::string why;
+    if (validate_config(cfg, why) != DEM_OK) return bfail(b, DEM_ERR_INVALID_ARG, why);
+    if (cfg->precision != b->d.precision || cfg->model != b->d.model || cfg->stiffness != b->d.stiffness)
+        return bfail(b, DEM_ERR_INVALID_ARG, "precision, model and stiffness must match the batch");
+    if (cfg->resort_interval != 1) return bfail(b, DEM_ERR_INVALID_ARG, "batches sort every step (resort_interval 1)");
+    if (nwalls < 0 || nwalls > DEM_MAX_WALLS || (nwalls > 0 && !walls)) return bfail(b, DEM_ERR_INVALID_ARG, "nwalls");
+    if (n < 0 || n > 0x7FFFFF00 || step_budget < 0) return bfail(b, DEM_ERR_INVALID_ARG, "n or step_budget");
+    if (n > 0 && (!x || !v || !w || !r)) return bfail(b, DEM_ERR_INVALID_ARG, "x, v, w and r are required");
+    for (int k = 0; k < nwalls; ++k)
+        if (walls[k].kind == DEM_CYLINDER_IN && cfg->precision == DEM_FP32 && make_wall(walls[k]).axis < 0)
+            return bfail(b, DEM_ERR_INVALID_ARG, "in DEM_FP32 mode a cylinder axis must be a coordinate axis");
+    BatchScene sc;
+    sc.slot = b->next_slot++;
+    sc.cfg = *cfg;
+    sc.walls.assign(walls, walls + nwalls);
+    sc.n = n;
+    sc.budget = step_budget;
+    double rmax = 0.0;
+    for (int64_t k = 0; k < n; ++k) {
+        if (!(r[k] > 0.f) || !std::isfinite(r[k])) return bfail(b, DEM_ERR_INVALID_ARG, "radii must be finite and > 0");
+        if (!finite3(x + 3 * k) || !finite3(v + 3 * k) || !finite3(w + 3 * k))
+            return bfail(b, DEM_ERR_INVALID_ARG, "non-finite input");
+        rmax = std::max(rmax, (double)r[k]);
+    }
+    const double hmin = 2.0 * rmax * (1.0 + std::ldexp(1.0, -10)) + cfg->skin;
+    double hc = cfg->cell_size > 0.0 ? cfg->cell_size : hmin;
+    if (n > 0 && hc < hmin * (1.0 - 1e-12)) return bfail(b, DEM_ERR_INVALID_ARG, "cell_size too small");
+    if (!(hc > 0.0)) hc = 1.0;
+    int64_t nc = 1;
+    for (int a = 0; a < 3; ++a) {
+        sc.origin[a] = cfg->domain_lo[a];
+        sc.dims[a] = std::max<int64_t>(1, (int64_t)std::ceil((cfg->domain_hi[a] - cfg->domain_lo[a]) / hc));
+        nc *= sc.dims[a];
+        if (nc > (int64_t)0x7FFFFFFF) return bfail(b, DEM_ERR_INVALID_ARG, "grid has more than 2^31 cells");
+    }
+    sc.h = hc;
+    sc.rmax = rmax;
+    sc.ncell = (uint32_t)nc;
+    sc.x.assign(x, x + 3 * n);
+    sc.v.assign(v, v + 3 * n);
+    sc.w.assign(w, w + 3 * n);
+    sc.r.assign(r, r + n);
+    *slot = sc.slot;
+    b->scenes.push_back(std::move(sc));
+    b->dirty = true;
+    return DEM_OK;
+}
+
+dem_status dem_batch_remove(dem_batch* b, int slot) {
+    if (!b) return DEM_ERR_INVALID_ARG;
+    BatchScene* sc = find_slot(b, slot);
+    if (!sc) return bfail(b, DEM_ERR_INVALID_ARG, "no such slot");
+    sc->removed = true;
+    b->dirty = true;
+    return DEM_OK;
+}
+
+dem_status dem_batch_run(dem_batch* b, int64_t max_steps, int* finished, int cap, int* nfinished) {
+    if (!b || max_steps < 0 || (cap > 0 && !finished)) return DEM_ERR_INVALID_ARG;
+    if (b->broken) return bfail(b, DEM_ERR_STATE, "batch is unusable after a CUDA error");
+    DeviceGuard g(b->device);
+    if (nfinished) *nfinished = 0;
+    if (b->dirty) {
+        dem_status s = repack(b);
+        if (s != DEM_OK) return s;
+    }
+    Domain& d = b->d;
+    int64_t left = max_steps;
+    int nfin = 0;
+    while (left > 0) {
+        int64_t s = left;
+        bool any = false;
+        for (auto& sc : b->scenes)
+            if (sc.in_domain && sc.done < sc.budget) {
+                any = true;
+                s = std::min(s, sc.budget - sc.done);
+            }
+        if (!any) break;
+        BCK(b, run_steps(d, &b->graph, s));
+        left -= s;
+        bool changed = false;
+        for (size_t k = 0; k < b->scenes.size(); ++k) {
+            BatchScene& sc = b->scenes[k];
+            if (!sc.in_domain || sc.done >= sc.budget) continue;
+            sc.done += s;
+            if (sc.done >= sc.budget) {
+                if (nfin < cap) finished[nfin] = sc.slot;
+                ++nfin;
+                changed = true;
+            }
+        }
+        if (changed) {
+            // freeze the finished scenes (the scene table is device memory, so the
+            // captured graph stays valid)
+            for (size_t k = 0; k < b->scenes.size(); ++k)
+                d.h_scenes[k].active = b->scenes[k].done < b->scenes[k].budget ? 1 : 0;
+            BCK(b, cudaMemcpyAsync(d.d_scenes, d.h_scenes.data(), sizeof(SceneDev) * b->scenes.size(),
+                                   cudaMemcpyHostToDevice, d.stream));
+            break;   // hand control back so that the caller can read, remove and admit
+        }
+    }
+    if (nfinished) *nfinished = nfin;
+    BCK(b, cudaMemcpyAsync(d.st_host, d.st, sizeof(StatusDev), cudaMemcpyDeviceToHost, d.stream));
+    BCK(b, cudaStreamSynchronize(d.stream));
+    if (d.st_host->code != 0) {
+        const int code = d.st_host->code;
+        BCK(b, cudaMemsetAsync(d.st, 0, 2 * sizeof(int32_t), d.stream));
+        return bfail(b, code == ST_CAPACITY ? DEM_ERR_CAPACITY : DEM_ERR_NONFINITE, "device status raised");
+    }
+    return DEM_OK;
+}
+
+dem_status dem_batch_get_state(dem_batch* b, int slot, double* x, double* v, double* w, int where) {
+    if (!b || (where != DEM_HOST && where != DEM_DEVICE)) return DEM_ERR_INVALID_ARG;
+    if (b->broken) return bfail(b, DEM_ERR_STATE, "batch is unusable after a CUDA error");
+    BatchScene* sc = find_slot(b, slot);
+    if (!sc) return bfail(b, DEM_ERR_INVALID_ARG, "no such slot");
+    const size_t n = (size_t)sc->n;
+    if (!sc->in_domain) {
+        if (where != DEM_HOST) return bfail(b, DEM_ERR_STATE, "scene not yet in the domain: host read only");
+        if (x) std::copy(sc->x.begin(), sc->x.end(), x);
+        if (v) std::copy(sc->v.begin(), sc->v.end(), v);
+        if (w) std::copy(sc->w.begin(), sc->w.end(), w);
+        return DEM_OK;
+    }
+    DeviceGuard g(b->device);
+    Domain& d = b->d;
+    if (n == 0) return DEM_OK;
+    if (where == DEM_DEVICE) {
+        BCK(b, run_export_range(d, sc->p0, (uint32_t)n, x, v, w));
+    } else {
+        if (b->stage_cap < n) {
+            if (b->stage) cudaFree(b->stage);
+            if (b->stage_r) cudaFree(b->stage_r);
+            b->stage = nullptr;
+            b->stage_r = nullptr;
+            if (cudaMalloc(&b->stage, n * 72) != cudaSuccess || cudaMalloc(&b->stage_r, n * 4) != cudaSuccess) {
+                cudaGetLastError();
+                return bfail(b, DEM_ERR_OOM, "cudaMalloc(stage) failed");
+            }
+            b->stage_cap = n;
+        }
+        BCK(b, run_export_range(d, sc->p0, (uint32_t)n, x ? b->stage : nullptr, v ? b->stage + 3 * n : nullptr,
+                                w ? b->stage + 6 * n : nullptr));
+        if (x) BCK(b, cudaMemcpyAsync(x, b->stage, n * 24, cudaMemcpyDeviceToHost, d.stream));
+        if (v) BCK(b, cudaMemcpyAsync(v, b->stage + 3 * n, n * 24, cudaMemcpyDeviceToHost, d.stream));
+        if (w) BCK(b, cudaMemcpyAsync(w, b->stage + 6 * n, n * 24, cudaMemcpyDeviceToHost, d.stream));
+    }
+    BCK(b, cudaStreamSynchronize(d.stream));
+    return DEM_OK;
+}
+
+dem_status dem_batch_info(const dem_batch* b, int slot, int64_t* n, int64_t* steps_done, int64_t* budget) {
+    if (!b) return DEM_ERR_INVALID_ARG;
+    for (const auto& sc : b->scenes)
+        if (sc.slot == slot && !sc.removed) {
+            if (n) *n = sc.n;
+            if (steps_done) *steps_done = sc.done;
+            if (budget) *budget = sc.budget;
+            return DEM_OK;
+        }
+    return DEM_ERR_INVALID_ARG;
+}
+
+int64_t dem_batch_device_bytes(const dem_batch* b) {
+    if (!b) return 0;
+    const Domain& d = b->d;
+    const size_t N = d.cap, M = d.maxc, C = (size_t)d.cells_cap + 1;
+    const size_t T = d.precision == 0 ? 8 : 4;
+    const size_t state = d.precision == 0 ? N * (9 * 8 + 8) : N * (4 * 16 + 4);
+    return (int64_t)(2 * state + 2 * (N * 4 + N * 4 * M + N * T * 3 * M) + 5 * N * 4 + 2 * C * 4 +
+                     b->stage_cap * 76 + b->map_cap * 4);
+}
+
+int64_t dem_batch_launch_count(const dem_batch* b) { return b ? b->d.launches : 0; }
+
+const char* dem_batch_last_error(const dem_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void dem_batch_destroy(dem_batch* b) {
+    if (!b) return;
+    DeviceGuard g(b->device);
+    if (b->d.stream) cudaStreamSynchronize(b->d.stream);
+    else cudaDeviceSynchronize();
+    b->graph.reset();
+    free_particle_buffers(b->d);
+    if (b->d.d_scenes) cudaFree(b->d.d_scenes);
+    if (b->d.st) cudaFree(b->d.st);
+    if (b->d.st_host) cudaFreeHost(b->d.st_host);
+    if (b->d.ctrl) cudaFree(b->d.ctrl);
+    if (b->d.ctrl_host) cudaFreeHost(b->d.ctrl_host);
+    if (b->d.diag_out) cudaFree(b->d.diag_out);
+    if (b->stage) cudaFree(b->stage);
+    if (b->stage_r) cudaFree(b->stage_r);
+    if (b->d_map) cudaFree(b->d_map);
+    cudaGetLastError();
+    delete b;
 }
 
 }  // extern "C"

@@ -11,7 +11,16 @@
 
 #include "dem_domain.h"
 
+// Minimum resident 256-thread blocks per SM requested for the force kernel (caps its
+// registers at 65536 / (256 * value)).
+#ifndef DEM_FORCE_MIN_BLOCKS
+#define DEM_FORCE_MIN_BLOCKS 3
+#endif
+
 namespace demgb {
+
+// L1 prefetch (PTX prefetch.global.L1): starts a line fill without holding a register.
+__device__ __forceinline__ void prefetch_l1(const void* p) { asm volatile("prefetch.global.L1 [%0];" ::"l"(p)); }
 
 // ======================================================================= FP64 policy
 struct PF64 {
@@ -44,8 +53,55 @@ struct PF64 {
         w = mk(__ldg(&s.wx[j]), __ldg(&s.wy[j]), __ldg(&s.wz[j]));
     }
     // Contact iff d^2 < R^2 with d^2 = fma(dz,dz, fma(dy,dy, dx*dx)), R = r_i + r_j (exact).
-    static __device__ __forceinline__ bool contact(const State& s, const Self& me, uint32_t j, const SceneDev&,
-                                                   V3<double>& n, double& delta, float& rj) {
+    static __device__ __forceinline__ bool touches(const Self& me, double xj, double yj, double zj, float rjf) {
+        const double dx = __dsub_rn(xj, me.x), dy = __dsub_rn(yj, me.y), dz = __dsub_rn(zj, me.z);
+        const double d2 = __fma_rn(dz, dz, __fma_rn(dy, dy, __dmul_rn(dx, dx)));
+        const double R = __dadd_rn((double)me.r, (double)rjf);
+        return d2 < __dmul_rn(R, R);
+    }
+    // Phase 1 of the walk: append to the near list every particle of [j0, j1) in contact.
+    static __device__ __forceinline__ void scan_row(const State& s, const Self& me, const SceneDev&, uint32_t j0,
+                                                    uint32_t j1, uint32_t q, uint32_t* lst, uint32_t bd, uint32_t tid,
+                                                    uint32_t maxc, uint32_t& cnt) {
+        for (uint32_t j = j0; j < j1; ++j) {
+            if (j == q) continue;
+            if (touches(me, __ldg(&s.x[j]), __ldg(&s.y[j]), __ldg(&s.z[j]), __ldg(&s.r[j]))) {
+                if (cnt < maxc) lst[cnt * bd + tid] = j;
+                ++cnt;
+            }
+        }
+    }
+    // Phase 1 from a neighbour list built at the last sort.
+    static __device__ __forceinline__ void scan_list(const State& s, const Self& me, const SceneDev&,
+                                                     const uint32_t* nl, uint32_t m, size_t cap, uint32_t q,
+                                                     uint32_t* lst, uint32_t bd, uint32_t tid, uint32_t maxc,
+                                                     uint32_t& cnt) {
+        for (uint32_t k = 0; k < m; ++k) {
+            const uint32_t j = __ldg(&nl[k * cap + q]);
+            if (touches(me, __ldg(&s.x[j]), __ldg(&s.y[j]), __ldg(&s.z[j]), __ldg(&s.r[j]))) {
+                if (cnt < maxc) lst[cnt * bd + tid] = j;
+                ++cnt;
+            }
+        }
+    }
+    // Neighbour-list test: j may come within contact of i while both move less than
+    // skin/2 (FP32 on the rounded positions, conservative by eps).
+    static __device__ __forceinline__ bool within(const State& s, const Self& me, uint32_t j, float reach_extra) {
+        const float ax = (float)__ldg(&s.x[j]) - (float)me.x, ay = (float)__ldg(&s.y[j]) - (float)me.y,
+                    az = (float)__ldg(&s.z[j]) - (float)me.z;
+        const float Re = (__ldg(&s.r[j]) + me.r) + reach_extra;
+        return ax * ax + ay * ay + az * az < Re * Re;
+    }
+    static __device__ __forceinline__ float4 pos_f(const Self& m) {
+        return make_float4((float)m.x, (float)m.y, (float)m.z, 0.f);
+    }
+    static __device__ __forceinline__ void prefetch_partner(const State& s, uint32_t j) {
+        prefetch_l1(&s.vx[j]);
+        prefetch_l1(&s.wx[j]);
+    }
+    // Phase 2: geometry of a listed contact (the decision is the same as in scan_row).
+    static __device__ __forceinline__ bool exact(const State& s, const Self& me, uint32_t j, const SceneDev&,
+                                                 V3<double>& n, double& delta, float& rj) {
         const double dx = __dsub_rn(__ldg(&s.x[j]), me.x);
         const double dy = __dsub_rn(__ldg(&s.y[j]), me.y);
         const double dz = __dsub_rn(__ldg(&s.z[j]), me.z);
@@ -110,7 +166,7 @@ struct PF64 {
     // Semi-implicit Euler (Sec. 4.2 step 1): v' = v + F dt/m, w' = w + T dt/I, x' = x + v' dt.
     static __device__ __forceinline__ uint32_t integrate(const State& B, uint32_t q, const Self& me, V3<double> F,
                                                          V3<double> Tq, const SceneDev& S, double m, bool& clamped,
-                                                         bool& finite) {
+                                                         bool& finite, float4& pnew) {
         const double r = (double)me.r;
         const double I = 0.4 * m * r * r;
         const V3<double> vn = me.v + F * (S.dt / m);
@@ -122,6 +178,7 @@ struct PF64 {
         B.wx[q] = wn.x; B.wy[q] = wn.y; B.wz[q] = wn.z;
         B.id[q] = me.id;
         finite = isfinite(xn) && isfinite(yn) && isfinite(zn) && isfinite(vn.x) && isfinite(vn.y) && isfinite(vn.z);
+        pnew = make_float4((float)xn, (float)yn, (float)zn, 0.f);
         return cell_key(S, xn, yn, zn, clamped);
     }
     static __device__ __forceinline__ V3<double> pos(const Self& m) { return mk(m.x, m.y, m.z); }
@@ -167,14 +224,83 @@ struct PF32 {
         v = mk(a.x, a.y, a.z);
         w = mk(b.x, b.y, b.z);
     }
-    // FP32 prefilter on hi (conservative by eps_f), then the sign of R^2 - d^2 evaluated
-    // with error-free transformations (about 2^-46 relative to R^2).
-    static __device__ __forceinline__ bool contact(const State& s, const Self& me, uint32_t j, const SceneDev& S,
-                                                   V3<float>& n, float& delta, float& rj) {
+    // FP32 prefilter on hi: conservative by eps_f (it bounds the FP32 error of hi_j - hi_i
+    // and of the squared distance), so no pair in contact is ever rejected.
+    static __device__ __forceinline__ bool near(const Self& me, float4 pj, float eps) {
+        const float ax = pj.x - me.hx, ay = pj.y - me.hy, az = pj.z - me.hz;
+        const float Re = (pj.w + me.r) + eps;
+        return ax * ax + ay * ay + az * az < Re * Re;
+    }
+    // Phase 1 of the walk: append to the near list every particle of [j0, j1) that passes
+    // the prefilter (two candidates in flight per iteration).
+    static __device__ __forceinline__ void scan_row(const State& s, const Self& me, const SceneDev& S, uint32_t j0,
+                                                    uint32_t j1, uint32_t q, uint32_t* lst, uint32_t bd, uint32_t tid,
+                                                    uint32_t maxc, uint32_t& cnt) {
+        const float eps = S.eps_f;
+        uint32_t j = j0;
+        for (; j + 2 <= j1; j += 2) {
+            const float4 a = __ldg(&s.P0[j]), b = __ldg(&s.P0[j + 1]);
+            if (j != q && near(me, a, eps)) {
+                if (cnt < maxc) lst[cnt * bd + tid] = j;
+                ++cnt;
+            }
+            if (j + 1 != q && near(me, b, eps)) {
+                if (cnt < maxc) lst[cnt * bd + tid] = j + 1;
+                ++cnt;
+            }
+        }
+        if (j < j1 && j != q && near(me, __ldg(&s.P0[j]), eps)) {
+            if (cnt < maxc) lst[cnt * bd + tid] = j;
+            ++cnt;
+        }
+    }
+    // Phase 1 from a neighbour list built at the last sort (two candidates in flight).
+    static __device__ __forceinline__ void scan_list(const State& s, const Self& me, const SceneDev& S,
+                                                     const uint32_t* nl, uint32_t m, size_t cap, uint32_t q,
+                                                     uint32_t* lst, uint32_t bd, uint32_t tid, uint32_t maxc,
+                                                     uint32_t& cnt) {
+        const float eps = S.eps_f;
+        uint32_t k = 0;
+        for (; k + 2 <= m; k += 2) {
+            const uint32_t j0 = __ldg(&nl[k * cap + q]), j1 = __ldg(&nl[(k + 1) * cap + q]);
+            const float4 a = __ldg(&s.P0[j0]), b = __ldg(&s.P0[j1]);
+            if (near(me, a, eps)) {
+                if (cnt < maxc) lst[cnt * bd + tid] = j0;
+                ++cnt;
+            }
+            if (near(me, b, eps)) {
+                if (cnt < maxc) lst[cnt * bd + tid] = j1;
+                ++cnt;
+            }
+        }
+        if (k < m) {
+            const uint32_t j0 = __ldg(&nl[k * cap + q]);
+            if (near(me, __ldg(&s.P0[j0]), eps)) {
+                if (cnt < maxc) lst[cnt * bd + tid] = j0;
+                ++cnt;
+            }
+        }
+    }
+    // Neighbour-list test: j may come within contact of i while both move less than
+    // skin/2 (FP32 on hi, conservative by eps).
+    static __device__ __forceinline__ bool within(const State& s, const Self& me, uint32_t j, float reach_extra) {
         const float4 pj = __ldg(&s.P0[j]);
         const float ax = pj.x - me.hx, ay = pj.y - me.hy, az = pj.z - me.hz;
-        const float Re = (pj.w + me.r) + S.eps_f;
-        if (ax * ax + ay * ay + az * az >= Re * Re) return false;
+        const float Re = (pj.w + me.r) + reach_extra;
+        return ax * ax + ay * ay + az * az < Re * Re;
+    }
+    static __device__ __forceinline__ float4 pos_f(const Self& m) { return make_float4(m.hx, m.hy, m.hz, 0.f); }
+    // payload that phase 2 reads for a listed candidate
+    static __device__ __forceinline__ void prefetch_partner(const State& s, uint32_t j) {
+        prefetch_l1(&s.P1[j]);
+        prefetch_l1(&s.V[j]);
+        prefetch_l1(&s.W[j]);
+    }
+    // Phase 2: the sign of R^2 - d^2 evaluated with error-free transformations (about
+    // 2^-46 relative to R^2), then delta = (R^2 - d^2)/(R + d) and the unit normal.
+    static __device__ __forceinline__ bool exact(const State& s, const Self& me, uint32_t j, const SceneDev&,
+                                                 V3<float>& n, float& delta, float& rj) {
+        const float4 pj = __ldg(&s.P0[j]);
         const float4 lj = __ldg(&s.P1[j]);
         float sx, tx, sy, ty, sz, tz;
         ff_diff(pj.x, lj.x, me.hx, me.lx, sx, tx);
@@ -324,7 +450,7 @@ struct PF32 {
     }
     static __device__ __forceinline__ uint32_t integrate(const State& B, uint32_t q, const Self& me, V3<float> F,
                                                          V3<float> Tq, const SceneDev& S, float m, bool& clamped,
-                                                         bool& finite) {
+                                                         bool& finite, float4& pnew) {
         const float r = me.r;
         const float I = 0.4f * m * r * r;
         const V3<float> vn = me.v + F * (S.dt_f / m);
@@ -339,6 +465,7 @@ struct PF32 {
         B.W[q] = make_float4(wn.x, wn.y, wn.z, 0.f);
         B.id[q] = me.id;
         finite = isfinite(hx) && isfinite(hy) && isfinite(hz) && isfinite(vn.x) && isfinite(vn.y) && isfinite(vn.z);
+        pnew = make_float4(hx, hy, hz, 0.f);
         return cell_key(S, hx, hy, hz, clamped);
     }
     static __device__ __forceinline__ V3<double> pos(const Self& m) {
@@ -355,7 +482,13 @@ struct ForceArgs {
     int nscenes;
     uint32_t n, cap;
     int maxc, stiffness;
-    typename PR::State A, B;
+    typename PR::State S0, S1;   // the two state sets; ctrl->cur names the current one
+    CtrlDev* ctrl;
+    const uint32_t* ncnt;        // list mode: neighbour lists of the last sort
+    const uint32_t* nl;
+    const float4* ref;           // list mode: positions at the last sort
+    float thresh2;               // list mode: squared displacement that forces a sort
+    int interval;                // list mode: sort at least every `interval` steps (0: never forced)
     const uint32_t* skey;
     const uint32_t* cs;
     const uint32_t* perm;
@@ -373,166 +506,213 @@ struct ForceArgs {
     double* dbgT;
 };
 
-template <class PR, int MODEL, bool EVAL>
-__global__ void __launch_bounds__(256) k_force(ForceArgs<PR> a) {
+// Load the stored tangential spring of slot k (partner ids are in shared memory).
+template <class T>
+__device__ __forceinline__ V3<T> find_spring(const uint32_t* s_oid, uint32_t bd, uint32_t tid, uint32_t cnt_old,
+                                             uint32_t gid, const T* hin_d, size_t maxc, size_t cap, uint32_t src) {
+    for (uint32_t k = 0; k < cnt_old; ++k)
+        if (s_oid[k * bd + tid] == gid)
+            return mk(hin_d[(0 * maxc + k) * cap + src], hin_d[(1 * maxc + k) * cap + src],
+                      hin_d[(2 * maxc + k) * cap + src]);
+    return mk(T(0), T(0), T(0));
+}
+
+// One thread per cell-sorted particle. Phase 1 walks the 27 cells (Eq. 12) as 9 rows of
+// three x-adjacent cells and keeps the candidates that may touch in a per-thread list in
+// shared memory; phase 2 runs the lanes of a warp in lockstep over their lists (the warp
+// iterates max-list-length times instead of once per candidate), taking the contact
+// decision, the law (Eq. 1 or Eqs. 2-10) and the springs; then walls, gravity, the
+// update (step 1) and the new cell key with its rank in the cell (step 2).
+template <class PR, int MODEL, bool EVAL, bool LIST>
+__global__ void __launch_bounds__(256, DEM_FORCE_MIN_BLOCKS) k_force(ForceArgs<PR> a) {
     using T = typename PR::T;
-    extern __shared__ uint32_t s_oid[];   // [maxc][blockDim.x]: partner ids of the stored springs
+    extern __shared__ uint32_t smem[];
+    const int cur = a.ctrl->cur;
+    const typename PR::State A = cur ? a.S1 : a.S0;
+    const typename PR::State B = cur ? a.S0 : a.S1;
+    const bool pv = a.ctrl->perm_valid != 0;
+    if (LIST && !EVAL && blockIdx.x == 0 && threadIdx.x == 0 && a.interval > 0 && a.ctrl->since + 1 >= a.interval)
+        atomicOr(&a.ctrl->rebuild, 1);
     const uint32_t tid = threadIdx.x;
     const uint32_t bd = blockDim.x;
+    const uint32_t maxc = (uint32_t)a.maxc;
+    uint32_t* s_oid = smem;               // [maxc][bd] partner ids of the stored springs
+    uint32_t* s_near = smem + maxc * bd;  // [maxc][bd] near candidates of phase 1
     const uint32_t q = blockIdx.x * bd + tid;
+    const size_t cap = a.cap;
     uint32_t c_pp = 0, c_wc = 0, c_clamp = 0, c_nnew = 0;
     float c_maxov = 0.f;
-    if (q < a.n) {
-        const int si = scene_of(a.scenes, a.nscenes, q);
-        const SceneDev& S = a.scenes[si];
-        const typename PR::Self me = PR::load(a.A, q);
-        const uint32_t src = a.perm ? a.perm[q] : q;
-        const size_t cap = a.cap;
-        const int maxc = a.maxc;
-        uint32_t cnt_old = 0;
+    const bool valid = q < a.n;
+    const SceneDev& S = a.scenes[valid ? scene_of(a.scenes, a.nscenes, q) : 0];
+    const bool live = valid && S.active;
+    typename PR::Self me{};
+    uint32_t src = 0, cnt_old = 0, nnear = 0;
+    if (valid) {
+        me = PR::load(A, q);
+        src = pv ? a.perm[q] : q;
         if (MODEL == 0 || !S.active) {
-            cnt_old = min(a.hin_cnt[src], (uint32_t)maxc);
+            cnt_old = min(a.hin_cnt[src], maxc);
+            // the stored springs are streamed from DRAM: start their loads now so they are
+            // in L1 when phase 2 matches contacts against them
+            for (uint32_t k = 0; k < cnt_old; ++k)
+                for (int c = 0; c < 3; ++c) prefetch_l1(&a.hin_d[(c * (size_t)maxc + k) * cap + src]);
             for (uint32_t k = 0; k < cnt_old; ++k) s_oid[k * bd + tid] = a.hin_pid[k * cap + src];
         }
-        if (!S.active) {
-            // frozen scene: carry state and springs unchanged
-            if (!EVAL) {
-                PR::store(a.B, q, me);
-                for (uint32_t k = 0; k < cnt_old; ++k) {
-                    a.hout_pid[k * cap + q] = s_oid[k * bd + tid];
-                    for (int c = 0; c < 3; ++c)
-                        a.hout_d[(c * (size_t)maxc + k) * cap + q] = a.hin_d[(c * (size_t)maxc + k) * cap + src];
-                }
-                a.hout_cnt[q] = cnt_old;
+    }
+    if (valid && !live) {
+        // frozen scene: carry state and springs unchanged
+        if (!EVAL) {
+            PR::store(B, q, me);
+            for (uint32_t k = 0; k < cnt_old; ++k) {
+                a.hout_pid[k * cap + q] = s_oid[k * bd + tid];
+                for (int c = 0; c < 3; ++c)
+                    a.hout_d[(c * (size_t)maxc + k) * cap + q] = a.hin_d[(c * (size_t)maxc + k) * cap + src];
+            }
+            a.hout_cnt[q] = cnt_old;
+            if (!LIST) {
                 const uint32_t kk = a.skey[q];
                 a.key[q] = kk;
                 a.rank[q] = atomicAdd(&a.cnt[kk], 1u);
-            } else {
-                a.hout_cnt[q] = 0;
             }
         } else {
-            const Law<T> L = law_of(S, a.stiffness, T());
-            const T mi = PR::mass(S, me.r);
-            const T ri = (T)me.r;
-            const int nx = S.dims[0], ny = S.dims[1], nz = S.dims[2];
-            const uint32_t local = a.skey[q] - S.c0;
-            const int ix = (int)(local % (uint32_t)nx);
-            const uint32_t t1 = local / (uint32_t)nx;
-            const int iy = (int)(t1 % (uint32_t)ny);
-            const int iz = (int)(t1 / (uint32_t)ny);
-            V3<T> F = mk(T(0), T(0), T(0)), Tq = mk(T(0), T(0), T(0));
-            uint32_t nnew = 0;
-            // ---- particle-particle contacts: 27 cells (Eq. 12), as 9 rows of 3 contiguous cells
-            for (int dz = -1; dz <= 1; ++dz) {
-                const int z2 = iz + dz;
-                if (z2 < 0 || z2 >= nz) continue;
-                for (int dy = -1; dy <= 1; ++dy) {
-                    const int y2 = iy + dy;
-                    if (y2 < 0 || y2 >= ny) continue;
-                    const uint32_t rowbase = S.c0 + (uint32_t)((z2 * ny + y2) * nx);
-                    const uint32_t clo = rowbase + (uint32_t)max(ix - 1, 0);
-                    const uint32_t chi = rowbase + (uint32_t)min(ix + 1, nx - 1);
-                    const uint32_t j0 = __ldg(&a.cs[clo]), j1 = __ldg(&a.cs[chi + 1]);
-                    for (uint32_t j = j0; j < j1; ++j) {
-                        if (j == q) continue;
-                        V3<T> n;
-                        T delta;
-                        float rj;
-                        if (!PR::contact(a.A, me, j, S, n, delta, rj)) continue;
-                        const uint32_t gid = __ldg(&a.A.id[j]);
-                        V3<T> vj, wj;
-                        PR::load_vw(a.A, j, vj, wj);
-                        const V3<T> v = me.v - vj;
-                        if (MODEL == 0) {
-                            const T rjT = (T)rj;
-                            const V3<T> rw = mk(sym_madd(ri, me.w.x, rjT, wj.x), sym_madd(ri, me.w.y, rjT, wj.y),
-                                                sym_madd(ri, me.w.z, rjT, wj.z));
-                            const T mj = PR::mass(S, rj);
-                            const T meff = T(1) / (T(1) / mi + T(1) / mj);
-                            const T Reff = T(1) / (T(1) / ri + T(1) / rjT);
-                            V3<T> dold = mk(T(0), T(0), T(0));
-                            for (uint32_t k = 0; k < cnt_old; ++k)
-                                if (s_oid[k * bd + tid] == gid) {
-                                    dold = mk(a.hin_d[(0 * (size_t)maxc + k) * cap + src],
-                                              a.hin_d[(1 * (size_t)maxc + k) * cap + src],
-                                              a.hin_d[(2 * (size_t)maxc + k) * cap + src]);
-                                    break;
-                                }
-                            V3<T> Fc, Ftc, dnew;
-                            law_practical(L, n, delta, v, rw, Reff, meff, dold, Fc, Ftc, dnew);
-                            F = F + Fc;
-                            Tq = Tq + cross(n, Ftc) * ri;
-                            if (nnew < (uint32_t)maxc) {
-                                a.hout_pid[nnew * cap + q] = gid;
-                                a.hout_d[(0 * (size_t)maxc + nnew) * cap + q] = dnew.x;
-                                a.hout_d[(1 * (size_t)maxc + nnew) * cap + q] = dnew.y;
-                                a.hout_d[(2 * (size_t)maxc + nnew) * cap + q] = dnew.z;
-                            }
-                        } else {
-                            F = F + law_simple(L, n, delta, v);
-                            if (EVAL && nnew < (uint32_t)maxc) a.hout_pid[nnew * cap + q] = gid;
-                        }
-                        ++nnew;
-                        ++c_pp;
-                        c_maxov = fmaxf(c_maxov, (float)delta);
-                    }
+            a.hout_cnt[q] = 0;
+        }
+    }
+    // ---- phase 1: candidates that may touch. The 18 cell-start loads of the 9 rows are
+    // issued together before any candidate is read.
+    if (live && LIST) {
+        PR::scan_list(A, me, S, a.nl, min(__ldg(&a.ncnt[q]), 2 * maxc), cap, q, s_near, bd, tid, maxc, nnear);
+        if (nnear > maxc) raise_status(a.st, ST_CAPACITY, (int32_t)q);
+    } else if (live) {
+        const int nx = S.dims[0], ny = S.dims[1], nz = S.dims[2];
+        const uint32_t local = a.skey[q] - S.c0;
+        const int ix = (int)(local % (uint32_t)nx);
+        const uint32_t t1 = local / (uint32_t)nx;
+        const int iy = (int)(t1 % (uint32_t)ny);
+        const int iz = (int)(t1 / (uint32_t)ny);
+        const uint32_t xlo = (uint32_t)max(ix - 1, 0), xhi = (uint32_t)min(ix + 1, nx - 1) + 1;
+        uint32_t rlo[9], rhi[9];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) {
+            const int z2 = iz + r / 3 - 1, y2 = iy + r % 3 - 1;
+            const bool ok = z2 >= 0 && z2 < nz && y2 >= 0 && y2 < ny;
+            const uint32_t rowbase = S.c0 + (uint32_t)((z2 * ny + y2) * nx);
+            rlo[r] = ok ? __ldg(&a.cs[rowbase + xlo]) : 0u;
+            rhi[r] = ok ? __ldg(&a.cs[rowbase + xhi]) : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < 9; ++r)
+            PR::scan_row(A, me, S, rlo[r], rhi[r], q, s_near, bd, tid, maxc, nnear);
+        if (nnear > maxc) raise_status(a.st, ST_CAPACITY, (int32_t)q);
+    }
+    // ---- phase 2: contacts, in lockstep over the lists
+    const uint32_t mylen = min(nnear, maxc);
+    if (live)
+        for (uint32_t k = 0; k < mylen; ++k) PR::prefetch_partner(A, s_near[k * bd + tid]);
+    const uint32_t kmax = __reduce_max_sync(0xffffffffu, mylen);
+    V3<T> F = mk(T(0), T(0), T(0)), Tq = mk(T(0), T(0), T(0));
+    uint32_t nnew = 0;
+    T mi = T(0);
+    const T ri = (T)me.r;
+    Law<T> L{};
+    if (live) {
+        L = law_of(S, a.stiffness, T());
+        mi = PR::mass(S, me.r);
+    }
+    for (uint32_t k = 0; k < kmax; ++k) {
+        if (!(live && k < mylen)) continue;
+        const uint32_t j = s_near[k * bd + tid];
+        V3<T> n;
+        T delta;
+        float rj;
+        if (!PR::exact(A, me, j, S, n, delta, rj)) continue;
+        const uint32_t gid = __ldg(&A.id[j]);
+        V3<T> vj, wj;
+        PR::load_vw(A, j, vj, wj);
+        const V3<T> v = me.v - vj;
+        if (MODEL == 0) {
+            const T rjT = (T)rj;
+            const V3<T> rw = mk(sym_madd(ri, me.w.x, rjT, wj.x), sym_madd(ri, me.w.y, rjT, wj.y),
+                                sym_madd(ri, me.w.z, rjT, wj.z));
+            const T mj = PR::mass(S, rj);
+            const T meff = (mi * mj) / (mi + mj);
+            const T Reff = (ri * rjT) / (ri + rjT);
+            const V3<T> dold = find_spring(s_oid, bd, tid, cnt_old, gid, a.hin_d, (size_t)maxc, cap, src);
+            V3<T> Fc, Ftc, dnew;
+            law_practical(L, n, delta, v, rw, Reff, meff, dold, Fc, Ftc, dnew);
+            F = F + Fc;
+            Tq = Tq + cross(n, Ftc) * ri;
+            if (nnew < maxc) {
+                a.hout_pid[nnew * cap + q] = gid;
+                a.hout_d[(0 * (size_t)maxc + nnew) * cap + q] = dnew.x;
+                a.hout_d[(1 * (size_t)maxc + nnew) * cap + q] = dnew.y;
+                a.hout_d[(2 * (size_t)maxc + nnew) * cap + q] = dnew.z;
+            }
+        } else {
+            F = F + law_simple(L, n, delta, v);
+            if (EVAL && nnew < maxc) a.hout_pid[nnew * cap + q] = gid;
+        }
+        ++nnew;
+        ++c_pp;
+        c_maxov = fmaxf(c_maxov, (float)delta);
+    }
+    if (live) {
+        // ---- walls (step 8)
+        for (int w = 0; w < S.nwalls; ++w) {
+            const WallDev& W = S.walls[w];
+            V3<T> n, cp;
+            T delta;
+            if (!PR::wall(W, me, S, n, delta, cp)) continue;
+            const V3<T> v = me.v - PR::wall_vel(W, cp);
+            const uint32_t gid = DEM_WALL_BASE + (uint32_t)w;
+            if (MODEL == 0) {
+                const V3<T> rw = me.w * ri;
+                const V3<T> dold = find_spring(s_oid, bd, tid, cnt_old, gid, a.hin_d, (size_t)maxc, cap, src);
+                V3<T> Fc, Ftc, dnew;
+                law_practical(L, n, delta, v, rw, ri, mi, dold, Fc, Ftc, dnew);
+                F = F + Fc;
+                Tq = Tq + cross(n, Ftc) * ri;
+                if (nnew < maxc) {
+                    a.hout_pid[nnew * cap + q] = gid;
+                    a.hout_d[(0 * (size_t)maxc + nnew) * cap + q] = dnew.x;
+                    a.hout_d[(1 * (size_t)maxc + nnew) * cap + q] = dnew.y;
+                    a.hout_d[(2 * (size_t)maxc + nnew) * cap + q] = dnew.z;
                 }
-            }
-            // ---- walls (step 8)
-            for (int w = 0; w < S.nwalls; ++w) {
-                const WallDev& W = S.walls[w];
-                V3<T> n, cp;
-                T delta;
-                if (!PR::wall(W, me, S, n, delta, cp)) continue;
-                const V3<T> v = me.v - PR::wall_vel(W, cp);
-                const uint32_t gid = DEM_WALL_BASE + (uint32_t)w;
-                if (MODEL == 0) {
-                    const V3<T> rw = me.w * ri;
-                    V3<T> dold = mk(T(0), T(0), T(0));
-                    for (uint32_t k = 0; k < cnt_old; ++k)
-                        if (s_oid[k * bd + tid] == gid) {
-                            dold = mk(a.hin_d[(0 * (size_t)maxc + k) * cap + src],
-                                      a.hin_d[(1 * (size_t)maxc + k) * cap + src],
-                                      a.hin_d[(2 * (size_t)maxc + k) * cap + src]);
-                            break;
-                        }
-                    V3<T> Fc, Ftc, dnew;
-                    law_practical(L, n, delta, v, rw, ri, mi, dold, Fc, Ftc, dnew);
-                    F = F + Fc;
-                    Tq = Tq + cross(n, Ftc) * ri;
-                    if (nnew < (uint32_t)maxc) {
-                        a.hout_pid[nnew * cap + q] = gid;
-                        a.hout_d[(0 * (size_t)maxc + nnew) * cap + q] = dnew.x;
-                        a.hout_d[(1 * (size_t)maxc + nnew) * cap + q] = dnew.y;
-                        a.hout_d[(2 * (size_t)maxc + nnew) * cap + q] = dnew.z;
-                    }
-                } else {
-                    F = F + law_simple(L, n, delta, v);
-                    if (EVAL && nnew < (uint32_t)maxc) a.hout_pid[nnew * cap + q] = gid;
-                }
-                ++nnew;
-                ++c_wc;
-                c_maxov = fmaxf(c_maxov, (float)delta);
-            }
-            if (nnew > (uint32_t)maxc) raise_status(a.st, ST_CAPACITY, (int32_t)q);
-            c_nnew = nnew;
-            if (MODEL == 0 || EVAL) a.hout_cnt[q] = min(nnew, (uint32_t)maxc);
-            // gravity, once per particle
-            {
-                const T gx = sizeof(T) == 8 ? (T)S.g[0] : (T)S.g_f[0];
-                const T gy = sizeof(T) == 8 ? (T)S.g[1] : (T)S.g_f[1];
-                const T gz = sizeof(T) == 8 ? (T)S.g[2] : (T)S.g_f[2];
-                F = F + mk(gx, gy, gz) * mi;
-            }
-            if (EVAL) {
-                const size_t o = 3 * (size_t)me.id;
-                if (a.dbgF) { a.dbgF[o] = F.x; a.dbgF[o + 1] = F.y; a.dbgF[o + 2] = F.z; }
-                if (a.dbgT) { a.dbgT[o] = Tq.x; a.dbgT[o + 1] = Tq.y; a.dbgT[o + 2] = Tq.z; }
             } else {
-                bool clamped = false, finite = true;
-                const uint32_t kk = PR::integrate(a.B, q, me, F, Tq, S, mi, clamped, finite);
-                if (!finite) raise_status(a.st, ST_NONFINITE, (int32_t)q);
-                c_clamp = clamped ? 1u : 0u;
+                F = F + law_simple(L, n, delta, v);
+                if (EVAL && nnew < maxc) a.hout_pid[nnew * cap + q] = gid;
+            }
+            ++nnew;
+            ++c_wc;
+            c_maxov = fmaxf(c_maxov, (float)delta);
+        }
+        if (nnew > maxc) raise_status(a.st, ST_CAPACITY, (int32_t)q);
+        c_nnew = nnew;
+        if (MODEL == 0 || EVAL) a.hout_cnt[q] = min(nnew, maxc);
+        // gravity, once per particle
+        {
+            const T gx = sizeof(T) == 8 ? (T)S.g[0] : (T)S.g_f[0];
+            const T gy = sizeof(T) == 8 ? (T)S.g[1] : (T)S.g_f[1];
+            const T gz = sizeof(T) == 8 ? (T)S.g[2] : (T)S.g_f[2];
+            F = F + mk(gx, gy, gz) * mi;
+        }
+        if (EVAL) {
+            const size_t o = 3 * (size_t)me.id;
+            if (a.dbgF) { a.dbgF[o] = F.x; a.dbgF[o + 1] = F.y; a.dbgF[o + 2] = F.z; }
+            if (a.dbgT) { a.dbgT[o] = Tq.x; a.dbgT[o + 1] = Tq.y; a.dbgT[o + 2] = Tq.z; }
+        } else {
+            bool clamped = false, finite = true;
+            float4 pnew;
+            const uint32_t kk = PR::integrate(B, q, me, F, Tq, S, mi, clamped, finite, pnew);
+            if (!finite) raise_status(a.st, ST_NONFINITE, (int32_t)q);
+            c_clamp = clamped ? 1u : 0u;
+            if (LIST) {
+                // a particle that moved skin/2 (less the FP32 margin) since the last sort
+                // makes this step end with a sort and new lists
+                const float4 r0 = __ldg(&a.ref[q]);
+                const float ex = pnew.x - r0.x, ey = pnew.y - r0.y, ez = pnew.z - r0.z;
+                if (ex * ex + ey * ey + ez * ez > a.thresh2 || !finite) atomicOr(&a.ctrl->rebuild, 1);
+            } else {
                 a.key[q] = kk;
                 a.rank[q] = atomicAdd(&a.cnt[kk], 1u);
             }
@@ -559,8 +739,11 @@ constexpr int SCAN_THREADS = 256;
 constexpr int SCAN_ITEMS = 8;
 constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 
+// Every kernel of the sort takes the step control and does nothing when this step does
+// not sort (list mode between sorts).
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __restrict__ cnt, uint32_t m,
-                                                              uint32_t* __restrict__ part) {
+                                                              uint32_t* __restrict__ part, const CtrlDev* ctrl) {
+    if (!ctrl->rebuild) return;
     __shared__ uint32_t ws[SCAN_THREADS / 32];
     const uint32_t base = blockIdx.x * SCAN_TILE;
     uint32_t s = 0;
@@ -579,7 +762,8 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __
 }
 
 // exclusive scan of part[0..nb) in one block of 1024 threads
-__global__ void __launch_bounds__(1024) k_scan_spine(uint32_t* part, uint32_t nb) {
+__global__ void __launch_bounds__(1024) k_scan_spine(uint32_t* part, uint32_t nb, const CtrlDev* ctrl) {
+    if (!ctrl->rebuild) return;
     __shared__ uint32_t sh[1024];
     const uint32_t per = (nb + 1023) / 1024;
     const uint32_t b0 = threadIdx.x * per;
@@ -605,7 +789,9 @@ __global__ void __launch_bounds__(1024) k_scan_spine(uint32_t* part, uint32_t nb
 
 // cs[k] = exclusive prefix of cnt; cnt[k] = 0 for the next sort
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(uint32_t* __restrict__ cnt, uint32_t m,
-                                                            const uint32_t* __restrict__ part, uint32_t* __restrict__ cs) {
+                                                            const uint32_t* __restrict__ part, uint32_t* __restrict__ cs,
+                                                            const CtrlDev* ctrl) {
+    if (!ctrl->rebuild) return;
     __shared__ uint32_t ws[SCAN_THREADS / 32];
     const uint32_t base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
     uint32_t v[SCAN_ITEMS];
@@ -645,23 +831,26 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(uint32_t* __restrict
 }
 
 __global__ void k_scatter(uint32_t n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
-                          const uint32_t* __restrict__ cs, uint32_t* __restrict__ tmp) {
+                          const uint32_t* __restrict__ cs, uint32_t* __restrict__ tmp, const CtrlDev* ctrl) {
+    if (!ctrl->rebuild) return;
     const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q < n) tmp[cs[key[q]] + rank[q]] = q;
 }
 
 // (cell, id) order: a particle's place in its cell is the number of cell-mates with a
-// smaller id. Gathers the state from B (pre-sort order) into A.
+// smaller id. Gathers the state from the next set (pre-sort order) into the current one,
+// records the permutation, the cell of each sorted particle and (list mode) its position.
 template <class PR>
-__global__ void k_reorder(uint32_t n, typename PR::State A, typename PR::State B, const uint32_t* __restrict__ key,
-                          const uint32_t* __restrict__ cs, const uint32_t* __restrict__ tmp, uint32_t* __restrict__ perm,
-                          uint32_t* __restrict__ skey, StatusDev* st) {
+__global__ void k_reorder(uint32_t n, typename PR::State S0, typename PR::State S1, const CtrlDev* ctrl,
+                          const uint32_t* __restrict__ key, const uint32_t* __restrict__ cs,
+                          const uint32_t* __restrict__ tmp, uint32_t* __restrict__ perm, uint32_t* __restrict__ skey,
+                          float4* __restrict__ ref) {
+    if (!ctrl->rebuild) return;
     const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s == 0) {
-        st->last = st->live;
-        st->live = CountersDev{};
-    }
     if (s >= n) return;
+    const int cur = ctrl->cur;
+    const typename PR::State A = cur ? S1 : S0;
+    const typename PR::State B = cur ? S0 : S1;
     const uint32_t p = tmp[s];
     const uint32_t c = key[p];
     const uint32_t lo = cs[c], hi = cs[c + 1];
@@ -669,9 +858,73 @@ __global__ void k_reorder(uint32_t n, typename PR::State A, typename PR::State B
     uint32_t r = 0;
     for (uint32_t k = lo; k < hi; ++k) r += (B.id[tmp[k]] < idp) ? 1u : 0u;
     const uint32_t q = lo + r;
-    PR::store(A, q, PR::load(B, p));
+    const typename PR::Self m = PR::load(B, p);
+    PR::store(A, q, m);
     perm[q] = p;
     skey[q] = c;
+    if (ref) ref[q] = PR::pos_f(m);
+}
+
+// Neighbour lists of the sorted state (list mode): every particle of the 27 cells around
+// each particle (Eq. 12) that lies within r_i + r_j + skin (+ the FP32 margin). With
+// cells of edge >= 2 r_max + skin, no pair that comes into contact before some particle
+// has moved skin/2 is missed.
+template <class PR>
+__global__ void __launch_bounds__(256) k_nlist(uint32_t n, const SceneDev* scenes, int nscenes, typename PR::State S0,
+                                                typename PR::State S1, const CtrlDev* ctrl,
+                                                const uint32_t* __restrict__ skey, const uint32_t* __restrict__ cs,
+                                                uint32_t* __restrict__ ncnt, uint32_t* __restrict__ nl, size_t cap,
+                                                uint32_t maxn, float skin, StatusDev* st) {
+    if (!ctrl->rebuild) return;
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const typename PR::State A = ctrl->cur ? S1 : S0;
+    const SceneDev& S = scenes[scene_of(scenes, nscenes, q)];
+    const typename PR::Self me = PR::load(A, q);
+    const float extra = skin + S.eps_f;
+    const int nx = S.dims[0], ny = S.dims[1], nz = S.dims[2];
+    const uint32_t local = skey[q] - S.c0;
+    const int ix = (int)(local % (uint32_t)nx);
+    const uint32_t t1 = local / (uint32_t)nx;
+    const int iy = (int)(t1 % (uint32_t)ny);
+    const int iz = (int)(t1 / (uint32_t)ny);
+    const uint32_t xlo = (uint32_t)max(ix - 1, 0), xhi = (uint32_t)min(ix + 1, nx - 1) + 1;
+    uint32_t rlo[9], rhi[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        const int z2 = iz + r / 3 - 1, y2 = iy + r % 3 - 1;
+        const bool ok = z2 >= 0 && z2 < nz && y2 >= 0 && y2 < ny;
+        const uint32_t rowbase = S.c0 + (uint32_t)((z2 * ny + y2) * nx);
+        rlo[r] = ok ? __ldg(&cs[rowbase + xlo]) : 0u;
+        rhi[r] = ok ? __ldg(&cs[rowbase + xhi]) : 0u;
+    }
+    uint32_t m = 0;
+#pragma unroll
+    for (int r = 0; r < 9; ++r)
+        for (uint32_t j = rlo[r]; j < rhi[r]; ++j) {
+            if (j == q || !PR::within(A, me, j, extra)) continue;
+            if (m < maxn) nl[m * cap + q] = j;
+            ++m;
+        }
+    if (m > maxn) raise_status(st, ST_CAPACITY, (int32_t)q);
+    ncnt[q] = min(m, maxn);
+}
+
+// Step bookkeeping (one thread): after a sort the current set stays and springs are read
+// through the permutation next step; otherwise the next set becomes current.
+__global__ void k_end_step(CtrlDev* ctrl, StatusDev* st, int walk_mode) {
+    if (ctrl->rebuild) {
+        ctrl->perm_valid = 1;
+        ctrl->since = 0;
+        ctrl->nsorts += 1;
+    } else {
+        ctrl->cur ^= 1;
+        ctrl->perm_valid = 0;
+        ctrl->since += 1;
+    }
+    ctrl->rebuild = walk_mode;
+    st->last = st->live;
+    st->live = CountersDev{};
 }
 
 // ======================================================================= set-up / read-out
@@ -711,12 +964,15 @@ __global__ void k_import<PF32>(uint32_t n, StateF32 B, const double* __restrict_
     B.id[k] = k;
 }
 
+// Cell key CM (step 2) and the rank of each particle within its cell, for the next set.
 template <class PR>
-__global__ void k_hash_initial(uint32_t n, const SceneDev* scenes, int nscenes, typename PR::State B,
-                               uint32_t* __restrict__ key, uint32_t* __restrict__ rank, uint32_t* __restrict__ cnt,
-                               StatusDev* st) {
+__global__ void k_hash(uint32_t n, const SceneDev* scenes, int nscenes, typename PR::State S0, typename PR::State S1,
+                       const CtrlDev* ctrl, uint32_t* __restrict__ key, uint32_t* __restrict__ rank,
+                       uint32_t* __restrict__ cnt, StatusDev* st) {
+    if (!ctrl->rebuild) return;
     const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
+    const typename PR::State B = ctrl->cur ? S0 : S1;
     const SceneDev& S = scenes[scene_of(scenes, nscenes, q)];
     bool clamped = false;
     const uint32_t kk = PR::key_of(B, S, q, clamped);
@@ -726,12 +982,15 @@ __global__ void k_hash_initial(uint32_t n, const SceneDev* scenes, int nscenes, 
 }
 
 template <class PR>
-__global__ void k_export(uint32_t n, typename PR::State A, double* x, double* v, double* w);
+__global__ void k_export(uint32_t n, typename PR::State S0, typename PR::State S1, const CtrlDev* ctrl, double* x,
+                         double* v, double* w);
 
 template <>
-__global__ void k_export<PF64>(uint32_t n, StateF64 A, double* x, double* v, double* w) {
+__global__ void k_export<PF64>(uint32_t n, StateF64 S0, StateF64 S1, const CtrlDev* ctrl, double* x, double* v,
+                               double* w) {
     const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
+    const StateF64 A = ctrl->cur ? S1 : S0;
     const size_t o = 3 * (size_t)A.id[q];
     if (x) { x[o] = A.x[q]; x[o + 1] = A.y[q]; x[o + 2] = A.z[q]; }
     if (v) { v[o] = A.vx[q]; v[o + 1] = A.vy[q]; v[o + 2] = A.vz[q]; }
@@ -739,9 +998,11 @@ __global__ void k_export<PF64>(uint32_t n, StateF64 A, double* x, double* v, dou
 }
 
 template <>
-__global__ void k_export<PF32>(uint32_t n, StateF32 A, double* x, double* v, double* w) {
+__global__ void k_export<PF32>(uint32_t n, StateF32 S0, StateF32 S1, const CtrlDev* ctrl, double* x, double* v,
+                               double* w) {
     const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= n) return;
+    const StateF32 A = ctrl->cur ? S1 : S0;
     const size_t o = 3 * (size_t)A.id[q];
     if (x) {
         const float4 h = A.P0[q], l = A.P1[q];
@@ -759,8 +1020,10 @@ constexpr int NDIAG = 10;
 
 template <class PR>
 __global__ void __launch_bounds__(DIAG_THREADS) k_diag(uint32_t n, const SceneDev* scenes, int nscenes,
-                                                       typename PR::State A, double* __restrict__ part) {
+                                                       typename PR::State S0, typename PR::State S1,
+                                                       const CtrlDev* ctrl, double* __restrict__ part) {
     __shared__ double sh[NDIAG][DIAG_THREADS];
+    const typename PR::State A = ctrl->cur ? S1 : S0;
     const uint32_t tid = threadIdx.x;
     const uint32_t q = blockIdx.x * DIAG_THREADS + tid;
     double val[NDIAG];
@@ -811,6 +1074,62 @@ __global__ void __launch_bounds__(DIAG_THREADS) k_diag_final(const double* __res
         for (int k = 0; k < NDIAG; ++k) out[k] = sh[k][0];
 }
 
+
+// ======================================================================= batch repacking
+// Springs of the current state rewritten in cell-sorted order (index q), into the free
+// history buffer: afterwards slot lists sit at the same index as the particle.
+template <class T>
+__global__ void k_hist_canon(uint32_t n, const CtrlDev* ctrl, const uint32_t* __restrict__ perm,
+                             const uint32_t* __restrict__ cin, const uint32_t* __restrict__ pin,
+                             const T* __restrict__ din, uint32_t* __restrict__ cout, uint32_t* __restrict__ pout,
+                             T* __restrict__ dout, size_t cap, uint32_t maxc) {
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const uint32_t src = ctrl->perm_valid ? perm[q] : q;
+    const uint32_t c = min(cin[src], maxc);
+    cout[q] = c;
+    for (uint32_t k = 0; k < c; ++k) {
+        pout[k * cap + q] = pin[k * cap + src];
+        for (int a = 0; a < 3; ++a) dout[(a * (size_t)maxc + k) * cap + q] = din[(a * (size_t)maxc + k) * cap + src];
+    }
+}
+
+// New packed layout: particle p of the new domain takes the old current-state particle
+// map[p] (with its springs, already in sorted order) or, for map[p] == ~0, starts with
+// no springs (its state is imported separately).
+template <class PR>
+__global__ void k_repack(uint32_t n_new, const uint32_t* __restrict__ map, typename PR::State oS0,
+                         typename PR::State oS1, const CtrlDev* octrl, const uint32_t* __restrict__ ocnt,
+                         const uint32_t* __restrict__ opid, const typename PR::T* __restrict__ od, size_t ocap,
+                         typename PR::State nB, uint32_t* __restrict__ ncnt, uint32_t* __restrict__ npid,
+                         typename PR::T* __restrict__ nd, size_t ncap, uint32_t maxc) {
+    const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_new) return;
+    const uint32_t m = map[p];
+    if (m == 0xFFFFFFFFu) {
+        ncnt[p] = 0;
+        return;
+    }
+    const typename PR::State A = octrl->cur ? oS1 : oS0;
+    PR::store(nB, p, PR::load(A, m));
+    const uint32_t c = min(ocnt[m], maxc);
+    ncnt[p] = c;
+    for (uint32_t k = 0; k < c; ++k) {
+        npid[k * ncap + p] = opid[k * ocap + m];
+        for (int a = 0; a < 3; ++a) nd[(a * (size_t)maxc + k) * ncap + p] = od[(a * (size_t)maxc + k) * ocap + m];
+    }
+}
+
+static inline StateF64 shifted(StateF64 s, uint32_t p0) {
+    s.x += p0; s.y += p0; s.z += p0; s.vx += p0; s.vy += p0; s.vz += p0; s.wx += p0; s.wy += p0; s.wz += p0;
+    s.r += p0; s.id += p0;
+    return s;
+}
+static inline StateF32 shifted(StateF32 s, uint32_t p0) {
+    s.P0 += p0; s.P1 += p0; s.V += p0; s.W += p0; s.id += p0;
+    return s;
+}
+
 // ======================================================================= launchers
 static inline uint32_t nblk(uint32_t n, uint32_t b) { return (n + b - 1) / b; }
 
@@ -822,21 +1141,22 @@ static inline uint32_t nblk(uint32_t n, uint32_t b) { return (n + b - 1) / b; }
     } while (0)
 
 cudaError_t run_import(Domain& d, const double* x, const double* v, const double* w, const float* r) {
+    // the caller has set ctrl->cur = 0, so set 1 is the "next" set that the sort gathers from
     if (d.n == 0) return cudaSuccess;
-    if (d.precision == 0) k_import<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.B64, x, v, w, r);
-    else k_import<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.B32, x, v, w, r);
+    if (d.precision == 0) k_import<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.S64[1], x, v, w, r);
+    else k_import<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.S32[1], x, v, w, r);
     DEM_LAUNCH_CHECK();
     return cudaSuccess;
 }
 
-cudaError_t run_hash_initial(Domain& d) {
+cudaError_t run_hash(Domain& d) {
     if (d.n == 0) return cudaSuccess;
     if (d.precision == 0)
-        k_hash_initial<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.B64, d.key, d.rank,
-                                                                    d.cnt, d.st);
+        k_hash<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S64[0], d.S64[1], d.ctrl,
+                                                            d.key, d.rank, d.cnt, d.st);
     else
-        k_hash_initial<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.B32, d.key, d.rank,
-                                                                    d.cnt, d.st);
+        k_hash<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S32[0], d.S32[1], d.ctrl,
+                                                            d.key, d.rank, d.cnt, d.st);
     DEM_LAUNCH_CHECK();
     return cudaSuccess;
 }
@@ -845,25 +1165,44 @@ cudaError_t run_rebuild(Domain& d) {
     if (d.n == 0) return cudaSuccess;
     const uint32_t m = d.ncells + 1;
     const uint32_t nb = nblk(m, SCAN_TILE);
-    k_scan_reduce<<<nb, SCAN_THREADS, 0, d.stream>>>(d.cnt, m, d.part);
+    k_scan_reduce<<<nb, SCAN_THREADS, 0, d.stream>>>(d.cnt, m, d.part, d.ctrl);
     DEM_LAUNCH_CHECK();
-    k_scan_spine<<<1, 1024, 0, d.stream>>>(d.part, nb);
+    k_scan_spine<<<1, 1024, 0, d.stream>>>(d.part, nb, d.ctrl);
     DEM_LAUNCH_CHECK();
-    k_scan_down<<<nb, SCAN_THREADS, 0, d.stream>>>(d.cnt, m, d.part, d.cs);
+    k_scan_down<<<nb, SCAN_THREADS, 0, d.stream>>>(d.cnt, m, d.part, d.cs, d.ctrl);
     DEM_LAUNCH_CHECK();
-    k_scatter<<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.key, d.rank, d.cs, d.tmp);
+    k_scatter<<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.key, d.rank, d.cs, d.tmp, d.ctrl);
     DEM_LAUNCH_CHECK();
+    float4* ref = d.list_mode ? d.ref : nullptr;
     if (d.precision == 0)
-        k_reorder<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.A64, d.B64, d.key, d.cs, d.tmp, d.perm, d.skey, d.st);
+        k_reorder<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.S64[0], d.S64[1], d.ctrl, d.key, d.cs, d.tmp,
+                                                               d.perm, d.skey, ref);
     else
-        k_reorder<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.A32, d.B32, d.key, d.cs, d.tmp, d.perm, d.skey, d.st);
+        k_reorder<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.S32[0], d.S32[1], d.ctrl, d.key, d.cs, d.tmp,
+                                                               d.perm, d.skey, ref);
     DEM_LAUNCH_CHECK();
-    ++d.sorts;
+    if (d.list_mode) {
+        if (d.precision == 0)
+            k_nlist<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S64[0], d.S64[1], d.ctrl,
+                                                                 d.skey, d.cs, d.ncnt, d.nl, d.cap, (uint32_t)d.maxn,
+                                                                 d.skin_f, d.st);
+        else
+            k_nlist<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S32[0], d.S32[1], d.ctrl,
+                                                                 d.skey, d.cs, d.ncnt, d.nl, d.cap, (uint32_t)d.maxn,
+                                                                 d.skin_f, d.st);
+        DEM_LAUNCH_CHECK();
+    }
+    return cudaSuccess;
+}
+
+cudaError_t run_end_step(Domain& d) {
+    k_end_step<<<1, 1, 0, d.stream>>>(d.ctrl, d.st, d.list_mode ? 0 : 1);
+    DEM_LAUNCH_CHECK();
     return cudaSuccess;
 }
 
 template <class PR>
-static cudaError_t force_impl(Domain& d, const typename PR::State& A, const typename PR::State& B, bool eval,
+static cudaError_t force_impl(Domain& d, const typename PR::State& S0, const typename PR::State& S1, bool eval,
                               double* dbgF, double* dbgT) {
     ForceArgs<PR> a;
     a.scenes = d.d_scenes;
@@ -872,8 +1211,14 @@ static cudaError_t force_impl(Domain& d, const typename PR::State& A, const type
     a.cap = d.cap;
     a.maxc = d.maxc;
     a.stiffness = d.stiffness;
-    a.A = A;
-    a.B = B;
+    a.S0 = S0;
+    a.S1 = S1;
+    a.ctrl = d.ctrl;
+    a.ncnt = d.ncnt;
+    a.nl = d.nl;
+    a.ref = d.ref;
+    a.thresh2 = d.thresh2;
+    a.interval = d.interval;
     a.skey = d.skey;
     a.cs = d.cs;
     a.perm = d.perm;
@@ -891,29 +1236,94 @@ static cudaError_t force_impl(Domain& d, const typename PR::State& A, const type
     a.dbgF = dbgF;
     a.dbgT = dbgT;
     const uint32_t b = (uint32_t)d.block;
-    const size_t smem = (size_t)d.maxc * b * sizeof(uint32_t);
+    const size_t smem = 2 * (size_t)d.maxc * b * sizeof(uint32_t);
     const uint32_t g = nblk(d.n, b);
-    if (d.model == 0) {
-        if (eval) k_force<PR, 0, true><<<g, b, smem, d.stream>>>(a);
-        else k_force<PR, 0, false><<<g, b, smem, d.stream>>>(a);
+    auto launch = [&](auto kern) -> cudaError_t {
+        // lists of 2 x maxc ids per thread may exceed the 48 KB default of dynamic shared memory
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        kern<<<g, b, smem, d.stream>>>(a);
+        return cudaSuccess;
+    };
+    cudaError_t e;
+    if (d.list_mode) {
+        if (d.model == 0) e = eval ? launch(k_force<PR, 0, true, true>) : launch(k_force<PR, 0, false, true>);
+        else e = eval ? launch(k_force<PR, 1, true, true>) : launch(k_force<PR, 1, false, true>);
     } else {
-        if (eval) k_force<PR, 1, true><<<g, b, smem, d.stream>>>(a);
-        else k_force<PR, 1, false><<<g, b, smem, d.stream>>>(a);
+        if (d.model == 0) e = eval ? launch(k_force<PR, 0, true, false>) : launch(k_force<PR, 0, false, false>);
+        else e = eval ? launch(k_force<PR, 1, true, false>) : launch(k_force<PR, 1, false, false>);
     }
+    if (e != cudaSuccess) return e;
     DEM_LAUNCH_CHECK();
     return cudaSuccess;
 }
 
 cudaError_t run_force(Domain& d, bool eval, double* dbgF, double* dbgT) {
     if (d.n == 0) return cudaSuccess;
-    if (d.precision == 0) return force_impl<PF64>(d, d.A64, d.B64, eval, dbgF, dbgT);
-    return force_impl<PF32>(d, d.A32, d.B32, eval, dbgF, dbgT);
+    if (d.precision == 0) return force_impl<PF64>(d, d.S64[0], d.S64[1], eval, dbgF, dbgT);
+    return force_impl<PF32>(d, d.S32[0], d.S32[1], eval, dbgF, dbgT);
 }
 
 cudaError_t run_export(Domain& d, double* x, double* v, double* w) {
     if (d.n == 0) return cudaSuccess;
-    if (d.precision == 0) k_export<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.A64, x, v, w);
-    else k_export<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.A32, x, v, w);
+    if (d.precision == 0)
+        k_export<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.S64[0], d.S64[1], d.ctrl, x, v, w);
+    else
+        k_export<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.S32[0], d.S32[1], d.ctrl, x, v, w);
+    DEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+
+cudaError_t run_hist_canon(Domain& d) {
+    if (d.n == 0) return cudaSuccess;
+    const int hi = d.h_cur, ho = 1 - d.h_cur;
+    if (d.precision == 0)
+        k_hist_canon<double><<<nblk(d.n, 256), 256, 0, d.stream>>>(
+            d.n, d.ctrl, d.perm, d.hcnt[hi], d.hpid[hi], (const double*)d.hd[hi], d.hcnt[ho], d.hpid[ho],
+            (double*)d.hd[ho], d.cap, (uint32_t)d.maxc);
+    else
+        k_hist_canon<float><<<nblk(d.n, 256), 256, 0, d.stream>>>(
+            d.n, d.ctrl, d.perm, d.hcnt[hi], d.hpid[hi], (const float*)d.hd[hi], d.hcnt[ho], d.hpid[ho],
+            (float*)d.hd[ho], d.cap, (uint32_t)d.maxc);
+    DEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+cudaError_t run_repack(Domain& od, Domain& d, const uint32_t* map, uint32_t n_new) {
+    if (n_new == 0) return cudaSuccess;
+    const int ho = 1 - od.h_cur;   // canonical springs of the old domain (run_hist_canon)
+    if (d.precision == 0)
+        k_repack<PF64><<<nblk(n_new, 256), 256, 0, d.stream>>>(
+            n_new, map, od.S64[0], od.S64[1], od.ctrl, od.hcnt[ho], od.hpid[ho], (const double*)od.hd[ho], od.cap,
+            d.S64[1], d.hcnt[0], d.hpid[0], (double*)d.hd[0], d.cap, (uint32_t)d.maxc);
+    else
+        k_repack<PF32><<<nblk(n_new, 256), 256, 0, d.stream>>>(
+            n_new, map, od.S32[0], od.S32[1], od.ctrl, od.hcnt[ho], od.hpid[ho], (const float*)od.hd[ho], od.cap,
+            d.S32[1], d.hcnt[0], d.hpid[0], (float*)d.hd[0], d.cap, (uint32_t)d.maxc);
+    DEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+cudaError_t run_import_at(Domain& d, uint32_t p0, uint32_t np, const double* x, const double* v, const double* w,
+                          const float* r) {
+    if (np == 0) return cudaSuccess;
+    if (d.precision == 0) k_import<PF64><<<nblk(np, 256), 256, 0, d.stream>>>(np, shifted(d.S64[1], p0), x, v, w, r);
+    else k_import<PF32><<<nblk(np, 256), 256, 0, d.stream>>>(np, shifted(d.S32[1], p0), x, v, w, r);
+    DEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+cudaError_t run_export_range(Domain& d, uint32_t p0, uint32_t np, double* x, double* v, double* w) {
+    if (np == 0) return cudaSuccess;
+    if (d.precision == 0)
+        k_export<PF64><<<nblk(np, 256), 256, 0, d.stream>>>(np, shifted(d.S64[0], p0), shifted(d.S64[1], p0), d.ctrl,
+                                                             x, v, w);
+    else
+        k_export<PF32><<<nblk(np, 256), 256, 0, d.stream>>>(np, shifted(d.S32[0], p0), shifted(d.S32[1], p0), d.ctrl,
+                                                             x, v, w);
     DEM_LAUNCH_CHECK();
     return cudaSuccess;
 }
@@ -922,9 +1332,11 @@ cudaError_t run_diag(Domain& d) {
     const uint32_t nb = d.n ? nblk(d.n, DIAG_THREADS) : 1;
     if (d.n) {
         if (d.precision == 0)
-            k_diag<PF64><<<nb, DIAG_THREADS, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.A64, d.diag_part);
+            k_diag<PF64><<<nb, DIAG_THREADS, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S64[0], d.S64[1], d.ctrl,
+                                                             d.diag_part);
         else
-            k_diag<PF32><<<nb, DIAG_THREADS, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.A32, d.diag_part);
+            k_diag<PF32><<<nb, DIAG_THREADS, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S32[0], d.S32[1], d.ctrl,
+                                                             d.diag_part);
         DEM_LAUNCH_CHECK();
         k_diag_final<<<1, DIAG_THREADS, 0, d.stream>>>(d.diag_part, nb, d.diag_out);
         DEM_LAUNCH_CHECK();

@@ -52,7 +52,9 @@ _lib = None
 _EXPORTS = ["dem_create", "dem_set_particles", "dem_set_walls", "dem_step", "dem_get_state", "dem_get_forces",
             "dem_get_history", "dem_restore", "dem_get_diagnostics", "dem_debug_snapshot", "dem_get_grid",
             "dem_device_bytes", "dem_launch_count", "dem_last_error", "dem_destroy", "dem_set_timing",
-            "dem_get_phase_times", "dem_sort_cells_static"]
+            "dem_get_phase_times", "dem_sort_cells_static", "dem_batch_create", "dem_batch_add", "dem_batch_run",
+            "dem_batch_get_state", "dem_batch_remove", "dem_batch_info", "dem_batch_device_bytes",
+            "dem_batch_launch_count", "dem_batch_last_error", "dem_batch_destroy"]
 
 
 def lib_path() -> str:
@@ -81,6 +83,20 @@ def lib():
     L.dem_debug_snapshot.argtypes = [P, P, P, I64, P, ctypes.POINTER(I64)]
     L.dem_get_grid.argtypes = [P, P, P, P]
     L.dem_sort_cells_static.argtypes = [I64, P, P, ctypes.c_double, P, P, P, P, P]
+    L.dem_batch_create.argtypes = [I32, I32, I32, I32, I32, I32, P, ctypes.POINTER(P)]
+    L.dem_batch_add.argtypes = [P, ctypes.POINTER(dem_config), I32, P, I64, P, P, P, P, I64, ctypes.POINTER(I32)]
+    L.dem_batch_run.argtypes = [P, I64, P, I32, ctypes.POINTER(I32)]
+    L.dem_batch_get_state.argtypes = [P, I32, P, P, P, I32]
+    L.dem_batch_remove.argtypes = [P, I32]
+    L.dem_batch_info.argtypes = [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    L.dem_batch_device_bytes.argtypes = [P]
+    L.dem_batch_device_bytes.restype = I64
+    L.dem_batch_launch_count.argtypes = [P]
+    L.dem_batch_launch_count.restype = I64
+    L.dem_batch_last_error.argtypes = [P]
+    L.dem_batch_last_error.restype = ctypes.c_char_p
+    L.dem_batch_destroy.argtypes = [P]
+    L.dem_batch_destroy.restype = None
     L.dem_set_timing.argtypes = [P, I32]
     L.dem_get_phase_times.argtypes = [P, P]
     L.dem_device_bytes.argtypes = [P]
@@ -97,7 +113,9 @@ def lib():
                                                   "dem_get_state", "dem_get_forces", "dem_get_history", "dem_restore",
                                                   "dem_get_diagnostics", "dem_debug_snapshot", "dem_get_grid",
                                                   "dem_set_timing", "dem_get_phase_times",
-                                                  "dem_sort_cells_static"):
+                                                  "dem_sort_cells_static", "dem_batch_create", "dem_batch_add",
+                                                  "dem_batch_run", "dem_batch_get_state", "dem_batch_remove",
+                                                  "dem_batch_info"):
             f.restype = ctypes.c_int
     _lib = L
     return L
@@ -368,3 +386,74 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+# ------------------------------------------------------------------ batches
+def _bcheck(b, status):
+    if status != DEM_OK:
+        msg = lib().dem_batch_last_error(b).decode() if b else ""
+        raise DemError(status, msg)
+
+
+def dem_batch_create(precision="fp32", model="practical", stiffness="linear", max_contacts=0, block_size=0, device=0,
+                     cuda_stream=None):
+    b = ctypes.c_void_p()
+    st = lib().dem_batch_create({"fp64": DEM_FP64, "fp32": DEM_FP32}[precision],
+                                {"practical": DEM_PRACTICAL, "simple": DEM_SIMPLE}[model],
+                                {"linear": DEM_LINEAR, "hertz": DEM_HERTZ}[stiffness], max_contacts, block_size, device,
+                                ctypes.c_void_p(cuda_stream) if cuda_stream else None, ctypes.byref(b))
+    if st != DEM_OK:
+        raise DemError(st, "dem_batch_create rejected its arguments")
+    return b
+
+
+def dem_batch_add(b, params, x, v, w, r, step_budget):
+    n = len(r)
+    x = _host(x, np.float64, (n, 3)); v = _host(v, np.float64, (n, 3)); w = _host(w, np.float64, (n, 3))
+    r = _host(r, np.float32, (n,))
+    c = config_from_params(params)
+    walls = walls_array(params.walls)
+    slot = ctypes.c_int32(-1)
+    _bcheck(b, lib().dem_batch_add(b, ctypes.byref(c), len(params.walls), walls, n, _ptr(x), _ptr(v), _ptr(w),
+                                   _ptr(r), int(step_budget), ctypes.byref(slot)))
+    return slot.value
+
+
+def dem_batch_run(b, max_steps, cap=4096):
+    fin = np.zeros(max(cap, 1), np.int32)
+    nf = ctypes.c_int32(0)
+    _bcheck(b, lib().dem_batch_run(b, int(max_steps), _ptr(fin), cap, ctypes.byref(nf)))
+    return [int(k) for k in fin[:min(nf.value, cap)]]
+
+
+def dem_batch_get_state(b, slot, n):
+    x = np.zeros((n, 3)); v = np.zeros((n, 3)); w = np.zeros((n, 3))
+    _bcheck(b, lib().dem_batch_get_state(b, slot, _ptr(x), _ptr(v), _ptr(w), DEM_HOST))
+    return x, v, w
+
+
+def dem_batch_remove(b, slot):
+    _bcheck(b, lib().dem_batch_remove(b, slot))
+
+
+def dem_batch_info(b, slot):
+    n, done, budget = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _bcheck(b, lib().dem_batch_info(b, slot, ctypes.byref(n), ctypes.byref(done), ctypes.byref(budget)))
+    return n.value, done.value, budget.value
+
+
+def dem_batch_device_bytes(b):
+    return int(lib().dem_batch_device_bytes(b))
+
+
+def dem_batch_launch_count(b):
+    return int(lib().dem_batch_launch_count(b))
+
+
+def dem_batch_last_error(b):
+    return lib().dem_batch_last_error(b).decode()
+
+
+def dem_batch_destroy(b):
+    if b:
+        lib().dem_batch_destroy(b)

@@ -1,0 +1,59 @@
+"""Replicas and scene sharding over ranks (one process per GPU).
+
+A single scene is not partitioned across GPUs: that needs a halo exchange of the
+particles near each sub-domain face every step, which this library does not do.
+Independent scenes (a batch, or a stream of requests) are spread over ranks by device
+memory footprint, and every rank advances its own scenes with no collective in the data
+path. Only host-side figures are reduced: the slowest rank's time and the total
+particle count.
+"""
+from __future__ import annotations
+
+from typing import List, Sequence
+
+
+def shard_by_footprint(footprints: Sequence[float], world: int) -> List[List[int]]:
+    """Greedy longest-processing-time assignment: scenes in decreasing footprint (ties by
+    index) go to the rank with the smallest load so far (ties by rank). Deterministic, so
+    every rank computes the same assignment without communicating."""
+    if world < 1:
+        raise ValueError("world must be >= 1")
+    order = sorted(range(len(footprints)), key=lambda k: (-float(footprints[k]), k))
+    load = [0.0] * world
+    out: List[List[int]] = [[] for _ in range(world)]
+    for k in order:
+        r = min(range(world), key=lambda j: (load[j], j))
+        out[r].append(k)
+        load[r] += float(footprints[k])
+    for lst in out:
+        lst.sort()
+    return out
+
+
+def my_scenes(footprints: Sequence[float], rank: int, world: int) -> List[int]:
+    return shard_by_footprint(footprints, world)[rank]
+
+
+def _tensor(value, device):
+    import torch
+    return torch.tensor([float(value)], dtype=torch.float64, device=device)
+
+
+def reduce_max(value: float, device="cpu") -> float:
+    """Maximum over ranks (the slowest rank's time); identity without a process group."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = _tensor(value, device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, device="cpu") -> float:
+    """Sum over ranks (total particles advanced); identity without a process group."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = _tensor(value, device)
+    dist.all_reduce(t)
+    return float(t.item())

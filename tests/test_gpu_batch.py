@@ -1,0 +1,94 @@
+"""Batches: many scenes advanced by the same launches. Each scene's result must be the one
+it gets alone (bit for bit: the per-particle arithmetic and summation order do not depend
+on the other scenes), and scenes may join and leave between runs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1301_1714_gb300 import dem, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_1301_1714_gb300 import _build
+    _build.build()
+    dem.lib()
+    return torch
+
+
+def alone(sc, steps, stream=None):
+    with dem.Simulation(sc.params, sc.x, sc.v, sc.w, sc.r, cuda_stream=stream) as s:
+        s.step(steps)
+        return s.state()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_each_scene_in_the_mix_equals_the_scene_alone(torch_cuda, precision):
+    torch = torch_cuda
+    stream = torch.cuda.Stream()
+    mix = [scenes.box_lattice_n(seed=30 + k, n=n, e=e, mu=mu, precision=precision)
+           for k, (n, e, mu) in enumerate([(1024, 0.9, 0.3), (1500, 0.6, 0.5), (3000, 0.8, 0.1), (2048, 0.95, 0.6)])]
+    budgets = [60, 100, 100, 40]
+    b = dem.dem_batch_create(precision=precision, cuda_stream=stream.cuda_stream)
+    try:
+        slots = [dem.dem_batch_add(b, sc.params, sc.x, sc.v, sc.w, sc.r, bud) for sc, bud in zip(mix, budgets)]
+        done = []
+        for _ in range(10):
+            done += dem.dem_batch_run(b, 1000)
+            if len(done) == len(mix):
+                break
+        assert sorted(done) == sorted(slots)
+        for sc, sl, bud in zip(mix, slots, budgets):
+            n, steps_done, budget = dem.dem_batch_info(b, sl)
+            assert (n, steps_done, budget) == (sc.n, bud, bud)
+            xb, vb, wb = dem.dem_batch_get_state(b, sl, sc.n)
+            xa, va, wa = alone(sc, bud)
+            assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(wa, wb)
+    finally:
+        dem.dem_batch_destroy(b)
+
+
+def test_scenes_join_and_leave_between_runs(torch_cuda):
+    """Continuous batching: a scene admitted while others are mid-run, and a finished scene
+    removed, leave every other scene's trajectory unchanged."""
+    torch = torch_cuda
+    stream = torch.cuda.Stream()
+    A = scenes.box_lattice_n(seed=41, n=2000, precision="fp32")
+    B = scenes.box_lattice_n(seed=42, n=1200, precision="fp32", e=0.7)
+    C = scenes.drum(seed=43, n=2500)
+    b = dem.dem_batch_create(precision="fp32", cuda_stream=stream.cuda_stream)
+    try:
+        sa = dem.dem_batch_add(b, A.params, A.x, A.v, A.w, A.r, 150)
+        sb = dem.dem_batch_add(b, B.params, B.x, B.v, B.w, B.r, 50)
+        assert dem.dem_batch_run(b, 1000) == [sb]          # B finishes first, A is at 50
+        xb, _, _ = dem.dem_batch_get_state(b, sb, B.n)
+        dem.dem_batch_remove(b, sb)
+        sc_ = dem.dem_batch_add(b, C.params, C.x, C.v, C.w, C.r, 70)
+        assert dem.dem_batch_run(b, 1000) == [sc_]         # A at 120, C at 70
+        xc, _, _ = dem.dem_batch_get_state(b, sc_, C.n)
+        assert dem.dem_batch_run(b, 1000) == [sa]
+        xa, _, _ = dem.dem_batch_get_state(b, sa, A.n)
+        assert dem.dem_batch_run(b, 1000) == []
+    finally:
+        dem.dem_batch_destroy(b)
+    assert np.array_equal(xa, alone(A, 150)[0])
+    assert np.array_equal(xb, alone(B, 50)[0])
+    assert np.array_equal(xc, alone(C, 70)[0])
+    ref = oracle.State(A.params.copy(precision="fp64"), A.x, A.v, A.w, A.r).run(150)
+    assert np.max(np.abs(xa - ref.x)) <= 1e-9
+
+
+def test_graph_replay_equals_plain_launches(torch_cuda):
+    """dem_step on a non-default stream replays a captured two-step CUDA graph; the
+    result equals plain launches on the legacy stream bit for bit."""
+    torch = torch_cuda
+    stream = torch.cuda.Stream()
+    sc = scenes.box_rsa(seed=44, n=3000)
+    xa = alone(sc, 101)[0]
+    xb = alone(sc, 101, stream=stream.cuda_stream)[0]
+    assert np.array_equal(xa, xb)
