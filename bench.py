@@ -44,7 +44,7 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2000)
-    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["drum", "rsa", "box"], default="drum")
     ap.add_argument("--n", type=int, default=0, help="particle count (0 = the workload's own)")
@@ -52,10 +52,11 @@ def parse():
                     help="accelerated settling steps (input preparation, see settle_bed)")
     ap.add_argument("--relax", type=int, default=1000, help="steps at the real parameters after settling")
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--resort", type=int, default=1,
-                    help="cell-sort interval: 1 = every step (Sec. 4.2); 0 = when a particle moved skin/2; "
-                         "K > 1 = at least every K steps (both with neighbour lists)")
-    ap.add_argument("--skin-r", type=float, default=0.1, help="skin in mean radii (used when --resort != 1)")
+    ap.add_argument("--resort", type=str, default="tune",
+                    help="cell-sort policy: 'tune' = autotuned (block size, every step or skin-driven with "
+                         "neighbour lists); 1 = every step (Sec. 4.2); 0 = when a particle moved skin/2; K > 1 = "
+                         "at least every K steps")
+    ap.add_argument("--skin-r", type=float, default=0.1, help="skin in largest radii (used when --resort is 0 or K)")
     ap.add_argument("--simple-steps", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -82,8 +83,8 @@ def make_scene(args, rank=0):
     return scenes.box_lattice(seed=seed, precision="fp64")
 
 
-def workload_desc(args, sc):
-    p = sc.params
+def workload_desc(args, sc, p=None):
+    p = p or sc.params
     if args.workload == "drum":
         sort = ("sort every step" if p.resort_interval == 1 else
                 f"sort when a particle moved skin/2 (skin {p.skin * 1e3:.2f} mm), neighbour lists")
@@ -251,10 +252,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic_per_particle():
+def profiled_traffic_per_particle(list_mode=False):
     """DRAM bytes per particle of the force kernel from the committed ncu summary, if it
     was taken on the current kernel source (else None)."""
-    path = os.path.join(ROOT, "profiles", "force_kernel_drum.md")
+    path = os.path.join(ROOT, "profiles", "force_kernel_list_drum.md" if list_mode else "force_kernel_drum.md")
     try:
         txt = open(path).read()
     except OSError:
@@ -316,20 +317,38 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
 
     sc = make_scene(args, rank)
-    if args.resort != 1:
-        skin = args.skin_r * 1e-3
-        sc.params = sc.params.copy(resort_interval=args.resort, skin=skin, cell_size=sc.params.cell_size + skin)
-    p = sc.params
     N = sc.n
-    cfg = dem.config_from_params(p)
     t_prep = time.perf_counter()
     xs0, vs0, ws0 = settle_bed(dem, sc, dev.index, stream.cuda_stream, args.settle, args.relax)
+    if args.relax:
+        # relax at the real parameters (sort every step), then start every run from there
+        hr = dem.dem_create(dem.config_from_params(sc.params), dev.index, stream.cuda_stream)
+        try:
+            dem.dem_set_walls(hr, sc.params.walls)
+            dem.dem_set_particles(hr, xs0, vs0, ws0, sc.r)
+            dem.dem_step(hr, args.relax)
+            xs0, vs0, ws0 = dem.dem_get_state(hr, N)
+        finally:
+            dem.dem_destroy(hr)
+    rmax = float(sc.r.max())
+    tuned = None
+    if args.resort == "tune":
+        from paper_1301_1714_gb300 import autotune
+        best, table = autotune.tune(sc.params, xs0, vs0, ws0, sc.r, device=dev.index, cuda_stream=stream.cuda_stream)
+        p = autotune.apply(sc.params, rmax, best)
+        block = best.block
+        tuned = {"choice": {"block": best.block, "resort_interval": best.resort, "skin_frac_rmax": best.skin_frac},
+                 "table": [[c.block, c.resort, c.skin_frac, round(c.ms_per_step, 4)] for c in table]}
+    else:
+        k = int(args.resort)
+        block = 0
+        p = sc.params if k == 1 else sc.params.copy(resort_interval=k, skin=args.skin_r * rmax,
+                                                    cell_size=sc.params.cell_size + args.skin_r * rmax)
+    cfg = dem.config_from_params(p, block_size=block)
     h = dem.dem_create(cfg, dev.index, stream.cuda_stream)
     try:
         dem.dem_set_walls(h, p.walls)
         dem.dem_set_particles(h, xs0, vs0, ws0, sc.r)
-        if args.relax:
-            dem.dem_step(h, args.relax)
         t_prep = time.perf_counter() - t_prep
         dem.dem_step(h, max(3, args.warmup))
         # ---------------- timed region (device events on the library's stream)
@@ -368,15 +387,37 @@ def run_ours(args):
         sort_ms = phase[1] / max(phase[3], 1)
         peak, peak_src = measured_hbm_gbs()
         achieved = b_force * N / (force_ms / 1e3) / 1e9
-        bpp = profiled_traffic_per_particle()
+        bpp = profiled_traffic_per_particle(p.resort_interval != 1)
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": (round(bpp * N) if bpp else None),
-                "kernel": "k_force<PF32,practical>", "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "kernel": "k_force<PF32,practical,%s>" % ("list" if p.resort_interval != 1 else "walk"), "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_particle": round(b_force, 1), "Z": round(Z, 3), "W": round(W, 4),
                 "force_ms": round(force_ms, 4), "sort_ms": round(sort_ms, 4)}
 
-        # ---------------- practical / simple on the same settled bed
+        # ---------------- the paper's policy (sort and walk every step) on the same bed
         xs, vs, ws = dem.dem_get_state(h, N)
+        every = None
+        if p.resort_interval != 1:
+            hk = dem.dem_create(dem.config_from_params(sc.params), dev.index, stream.cuda_stream)
+            try:
+                dem.dem_set_walls(hk, sc.params.walls)
+                dem.dem_set_particles(hk, xs, vs, ws, sc.r)
+                dem.dem_step(hk, 3)
+                dem.dem_set_timing(hk, True)
+                k0 = torch.cuda.Event(enable_timing=True)
+                k1 = torch.cuda.Event(enable_timing=True)
+                k0.record(stream)
+                dem.dem_step(hk, args.simple_steps or 200)
+                k1.record(stream)
+                torch.cuda.synchronize(dev)
+                kms = k0.elapsed_time(k1) / (args.simple_steps or 200)
+                kph = dem.dem_get_phase_times(hk)
+                every = {"value": round(N / (kms / 1e3), 1), "ms_per_step": round(kms, 4),
+                         "force_ms": round(kph[0] / max(kph[2], 1), 4), "sort_ms": round(kph[1] / max(kph[3], 1), 4)}
+            finally:
+                dem.dem_destroy(hk)
+
+        # ---------------- practical / simple on the same settled bed
         simple = None
         if args.simple_steps > 0:
             hs = dem.dem_create(dem.config_from_params(p.copy(model="simple")), dev.index, stream.cuda_stream)
@@ -437,14 +478,14 @@ def run_ours(args):
         out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-               "config": {"workload": workload_desc(args, sc), "n_particles": N, "seed": args.seed,
+               "config": {"workload": workload_desc(args, sc, p), "n_particles": N, "seed": args.seed,
                           "settle_steps": args.settle, "relax_steps": args.relax, "prep_s": round(t_prep, 1),
                           "resort_interval": p.resort_interval, "skin_m": p.skin,
                           "sorts_in_timed_steps": int(sorts_timed),
                           "l2": "inputs larger than L2 (no flush needed)",
                           "device_bytes": dem.dem_device_bytes(h), "parallelism": f"replicas x{world}"},
                "roofline": roof, "gpu_launches": int(launches), "clocks": clocks, "simple": simple, "e2e": e2e,
-               "batch": batch, "serving": serving,
+               "batch": batch, "serving": serving, "autotune": tuned, "sort_every_step": every,
                "diagnostics": {k: diag[k] for k in ("pair_contacts", "wall_contacts", "max_overlap", "ke_trans")}}
     finally:
         dem.dem_destroy(h)

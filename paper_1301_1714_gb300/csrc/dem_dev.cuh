@@ -103,6 +103,23 @@ template <class T> __device__ __forceinline__ V3<T> cross(V3<T> a, V3<T> b) {
 __device__ __forceinline__ float dsqrt(float a) { return sqrtf(a); }
 __device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
 
+// Quotient and square root of the contact law. FP64 mode: IEEE operations. FP32 mode: the
+// hardware approximations (PTX div.approx / sqrt.approx, relative error about 2^-22),
+// well inside the FP32 mode's force tolerance; both are deterministic functions of their
+// arguments, so the two evaluations of a pair stay exact mirrors of each other.
+__device__ __forceinline__ double law_div(double a, double b) { return a / b; }
+__device__ __forceinline__ double law_sqrt(double a) { return sqrt(a); }
+__device__ __forceinline__ float law_div(float a, float b) {
+    float r;
+    asm("div.approx.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float law_sqrt(float a) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
+
 // Symmetric in (a1, b1) <-> (a2, b2): products rounded first, then one rounded sum, so the
 // two threads that evaluate the same pair get the same bits.
 __device__ __forceinline__ float sym_madd(float a1, float b1, float a2, float b2) {
@@ -161,17 +178,21 @@ __device__ __forceinline__ void law_practical(const Law<T>& P, V3<T> n, T delta,
     T kn, kt;                                                    // Eqs. 8-9
     if (P.stiffness == 0) { kn = P.kn; kt = P.kt; }
     else {
-        const T s = dsqrt(delta * Reff);
+        const T s = law_sqrt(delta * Reff);
         kn = P.cn * s;
         kt = P.ct * s;
     }
-    const T eta = P.alpha * dsqrt(kn * meff);                   // Eq. 10
+    const T eta = P.alpha * law_sqrt(kn * meff);                 // Eq. 10
     const V3<T> Fn = n * (-kn * delta) - vn * eta;               // Eq. 4
     V3<T> Ftt = dt * (-kt) - vt * eta;
-    const T ftn = dsqrt(dot(Ftt, Ftt)), fnn = dsqrt(dot(Fn, Fn));
-    if (ftn > P.mu * fnn && ftn > T(0)) {                        // Eq. 5
-        Ftt = Ftt * (P.mu * fnn / ftn);
-        if (kt > T(0)) dt = (Ftt + vt * eta) * (T(-1) / kt);
+    // Eq. 5, compared on squared lengths; the lengths are taken only when the cap applies
+    const T ft2 = dot(Ftt, Ftt), fn2 = dot(Fn, Fn);
+    if (ft2 > (P.mu * P.mu) * fn2 && ft2 > T(0)) {
+        const T ftn = law_sqrt(ft2), fnn = law_sqrt(fn2);
+        if (ftn > P.mu * fnn) {
+            Ftt = Ftt * law_div(P.mu * fnn, ftn);
+            if (kt > T(0)) dt = (Ftt + vt * eta) * law_div(T(-1), kt);
+        }
     }
     F = Fn + Ftt;                                                // Eq. 2
     Ft = Ftt;

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -203,6 +204,13 @@ dem_status validate_config(const dem_config* c, std::string& why) {
 dem_status alloc_domain(Domain& d, uint32_t n, uint32_t ncells, std::string& err) {
     const uint32_t need = std::max<uint32_t>(n, 1);
     if (need <= d.cap && ncells <= d.cells_cap) return DEM_OK;
+    // host-side fault injection for tests: DEM_FAULT=alloc makes every allocation of
+    // particle buffers fail as if the device were out of memory
+    const char* fault = std::getenv("DEM_FAULT");
+    if (fault && std::strstr(fault, "alloc")) {
+        err = "injected allocation failure (DEM_FAULT=alloc)";
+        return DEM_ERR_OOM;
+    }
     free_particle_buffers(d);
     const uint32_t cap = std::max<uint32_t>(need, 64);
     const uint32_t ccap = std::max<uint32_t>(ncells, 1);

@@ -71,18 +71,16 @@ struct PF64 {
             }
         }
     }
-    // Phase 1 from a neighbour list built at the last sort.
-    static __device__ __forceinline__ void scan_list(const State& s, const Self& me, const SceneDev&,
-                                                     const uint32_t* nl, uint32_t m, size_t cap, uint32_t q,
-                                                     uint32_t* lst, uint32_t bd, uint32_t tid, uint32_t maxc,
-                                                     uint32_t& cnt) {
+    // Phase 1 from a neighbour list built at the last sort: bit k of the returned mask
+    // marks list entry k as in contact.
+    static __device__ __forceinline__ uint64_t scan_list(const State& s, const Self& me, const SceneDev&,
+                                                         const uint32_t* nl, uint32_t m, size_t cap, uint32_t q) {
+        uint64_t mask = 0;
         for (uint32_t k = 0; k < m; ++k) {
             const uint32_t j = __ldg(&nl[k * cap + q]);
-            if (touches(me, __ldg(&s.x[j]), __ldg(&s.y[j]), __ldg(&s.z[j]), __ldg(&s.r[j]))) {
-                if (cnt < maxc) lst[cnt * bd + tid] = j;
-                ++cnt;
-            }
+            if (touches(me, __ldg(&s.x[j]), __ldg(&s.y[j]), __ldg(&s.z[j]), __ldg(&s.r[j]))) mask |= 1ull << k;
         }
+        return mask;
     }
     // Neighbour-list test: j may come within contact of i while both move less than
     // skin/2 (FP32 on the rounded positions, conservative by eps).
@@ -254,32 +252,33 @@ struct PF32 {
             ++cnt;
         }
     }
-    // Phase 1 from a neighbour list built at the last sort (two candidates in flight).
-    static __device__ __forceinline__ void scan_list(const State& s, const Self& me, const SceneDev& S,
-                                                     const uint32_t* nl, uint32_t m, size_t cap, uint32_t q,
-                                                     uint32_t* lst, uint32_t bd, uint32_t tid, uint32_t maxc,
-                                                     uint32_t& cnt) {
+    // Phase 1 from a neighbour list built at the last sort: bit k of the returned mask
+    // marks list entry k as passing the prefilter (two candidates in flight).
+    static __device__ __forceinline__ uint64_t scan_list(const State& s, const Self& me, const SceneDev& S,
+                                                         const uint32_t* nl, uint32_t m, size_t cap, uint32_t q) {
         const float eps = S.eps_f;
+        uint64_t mask = 0;
         uint32_t k = 0;
         for (; k + 2 <= m; k += 2) {
             const uint32_t j0 = __ldg(&nl[k * cap + q]), j1 = __ldg(&nl[(k + 1) * cap + q]);
             const float4 a = __ldg(&s.P0[j0]), b = __ldg(&s.P0[j1]);
             if (near(me, a, eps)) {
-                if (cnt < maxc) lst[cnt * bd + tid] = j0;
-                ++cnt;
+                mask |= 1ull << k;
+                prefetch_partner(s, j0);
             }
             if (near(me, b, eps)) {
-                if (cnt < maxc) lst[cnt * bd + tid] = j1;
-                ++cnt;
+                mask |= 1ull << (k + 1);
+                prefetch_partner(s, j1);
             }
         }
         if (k < m) {
             const uint32_t j0 = __ldg(&nl[k * cap + q]);
             if (near(me, __ldg(&s.P0[j0]), eps)) {
-                if (cnt < maxc) lst[cnt * bd + tid] = j0;
-                ++cnt;
+                mask |= 1ull << k;
+                prefetch_partner(s, j0);
             }
         }
+        return mask;
     }
     // Neighbour-list test: j may come within contact of i while both move less than
     // skin/2 (FP32 on hi, conservative by eps).
@@ -328,10 +327,10 @@ struct PF32 {
         low = __fsub_rn(low, __fadd_rn(__fadd_rn(cx, cy), cz));
         const float D = __fadd_rn(a3, low);
         if (!(D > 0.f)) return false;
-        const float d = sqrtf(__fadd_rn(__fadd_rn(px, py), pz));
-        delta = __fdiv_rn(D, __fadd_rn(Rh, d));
+        const float d = law_sqrt(__fadd_rn(__fadd_rn(px, py), pz));
+        delta = law_div(D, __fadd_rn(Rh, d));
         const float dc = __fadd_rn(__fsub_rn(Rh, delta), Rl);
-        const float inv = __fdiv_rn(1.f, dc);
+        const float inv = law_div(1.f, dc);
         n = mk(__fmul_rn(__fadd_rn(sx, tx), inv), __fmul_rn(__fadd_rn(sy, ty), inv), __fmul_rn(__fadd_rn(sz, tz), inv));
         rj = pj.w;
         return true;
@@ -537,7 +536,8 @@ __global__ void __launch_bounds__(256, DEM_FORCE_MIN_BLOCKS) k_force(ForceArgs<P
     const uint32_t bd = blockDim.x;
     const uint32_t maxc = (uint32_t)a.maxc;
     uint32_t* s_oid = smem;               // [maxc][bd] partner ids of the stored springs
-    uint32_t* s_near = smem + maxc * bd;  // [maxc][bd] near candidates of phase 1
+    uint32_t* s_near = smem + maxc * bd;  // [maxc][bd] near candidates of phase 1 (walk mode)
+    uint64_t near_mask = 0;               // list mode: list entries that passed phase 1
     const uint32_t q = blockIdx.x * bd + tid;
     const size_t cap = a.cap;
     uint32_t c_pp = 0, c_wc = 0, c_clamp = 0, c_nnew = 0;
@@ -581,8 +581,8 @@ __global__ void __launch_bounds__(256, DEM_FORCE_MIN_BLOCKS) k_force(ForceArgs<P
     // ---- phase 1: candidates that may touch. The 18 cell-start loads of the 9 rows are
     // issued together before any candidate is read.
     if (live && LIST) {
-        PR::scan_list(A, me, S, a.nl, min(__ldg(&a.ncnt[q]), 2 * maxc), cap, q, s_near, bd, tid, maxc, nnear);
-        if (nnear > maxc) raise_status(a.st, ST_CAPACITY, (int32_t)q);
+        near_mask = PR::scan_list(A, me, S, a.nl, min(__ldg(&a.ncnt[q]), 2 * maxc), cap, q);
+        nnear = __popcll(near_mask);
     } else if (live) {
         const int nx = S.dims[0], ny = S.dims[1], nz = S.dims[2];
         const uint32_t local = a.skey[q] - S.c0;
@@ -606,8 +606,8 @@ __global__ void __launch_bounds__(256, DEM_FORCE_MIN_BLOCKS) k_force(ForceArgs<P
         if (nnear > maxc) raise_status(a.st, ST_CAPACITY, (int32_t)q);
     }
     // ---- phase 2: contacts, in lockstep over the lists
-    const uint32_t mylen = min(nnear, maxc);
-    if (live)
+    const uint32_t mylen = LIST ? nnear : min(nnear, maxc);
+    if (live && !LIST)
         for (uint32_t k = 0; k < mylen; ++k) PR::prefetch_partner(A, s_near[k * bd + tid]);
     const uint32_t kmax = __reduce_max_sync(0xffffffffu, mylen);
     V3<T> F = mk(T(0), T(0), T(0)), Tq = mk(T(0), T(0), T(0));
@@ -619,9 +619,17 @@ __global__ void __launch_bounds__(256, DEM_FORCE_MIN_BLOCKS) k_force(ForceArgs<P
         L = law_of(S, a.stiffness, T());
         mi = PR::mass(S, me.r);
     }
+    uint64_t mask_left = near_mask;
     for (uint32_t k = 0; k < kmax; ++k) {
         if (!(live && k < mylen)) continue;
-        const uint32_t j = s_near[k * bd + tid];
+        uint32_t j;
+        if (LIST) {
+            const int e = __ffsll((long long)mask_left) - 1;
+            mask_left &= mask_left - 1;
+            j = __ldg(&a.nl[(size_t)e * cap + q]);
+        } else {
+            j = s_near[k * bd + tid];
+        }
         V3<T> n;
         T delta;
         float rj;
@@ -635,8 +643,8 @@ __global__ void __launch_bounds__(256, DEM_FORCE_MIN_BLOCKS) k_force(ForceArgs<P
             const V3<T> rw = mk(sym_madd(ri, me.w.x, rjT, wj.x), sym_madd(ri, me.w.y, rjT, wj.y),
                                 sym_madd(ri, me.w.z, rjT, wj.z));
             const T mj = PR::mass(S, rj);
-            const T meff = (mi * mj) / (mi + mj);
-            const T Reff = (ri * rjT) / (ri + rjT);
+            const T meff = law_div(mi * mj, mi + mj);
+            const T Reff = law_div(ri * rjT, ri + rjT);
             const V3<T> dold = find_spring(s_oid, bd, tid, cnt_old, gid, a.hin_d, (size_t)maxc, cap, src);
             V3<T> Fc, Ftc, dnew;
             law_practical(L, n, delta, v, rw, Reff, meff, dold, Fc, Ftc, dnew);
@@ -1236,7 +1244,7 @@ static cudaError_t force_impl(Domain& d, const typename PR::State& S0, const typ
     a.dbgF = dbgF;
     a.dbgT = dbgT;
     const uint32_t b = (uint32_t)d.block;
-    const size_t smem = 2 * (size_t)d.maxc * b * sizeof(uint32_t);
+    const size_t smem = (d.list_mode ? 1 : 2) * (size_t)d.maxc * b * sizeof(uint32_t);
     const uint32_t g = nblk(d.n, b);
     auto launch = [&](auto kern) -> cudaError_t {
         // lists of 2 x maxc ids per thread may exceed the 48 KB default of dynamic shared memory

@@ -92,3 +92,42 @@ def test_graph_replay_equals_plain_launches(torch_cuda):
     xa = alone(sc, 101)[0]
     xb = alone(sc, 101, stream=stream.cuda_stream)[0]
     assert np.array_equal(xa, xb)
+
+
+def test_cancelled_scene_leaves_others_unchanged(torch_cuda):
+    """A request cancelled mid-run (removed before its budget) does not disturb the rest."""
+    torch = torch_cuda
+    stream = torch.cuda.Stream()
+    A = scenes.box_lattice_n(seed=51, n=1800, precision="fp32")
+    B = scenes.box_lattice_n(seed=52, n=2600, precision="fp32", mu=0.5)
+    b = dem.dem_batch_create(precision="fp32", cuda_stream=stream.cuda_stream)
+    try:
+        sa = dem.dem_batch_add(b, A.params, A.x, A.v, A.w, A.r, 120)
+        sb = dem.dem_batch_add(b, B.params, B.x, B.v, B.w, B.r, 500)
+        assert dem.dem_batch_run(b, 40) == []
+        dem.dem_batch_remove(b, sb)                        # cancelled at step 40 of 500
+        assert dem.dem_batch_run(b, 1000) == [sa]
+        xa, _, _ = dem.dem_batch_get_state(b, sa, A.n)
+        with pytest.raises(dem.DemError):
+            dem.dem_batch_get_state(b, sb, B.n)
+    finally:
+        dem.dem_batch_destroy(b)
+    assert np.array_equal(xa, alone(A, 120)[0])
+
+
+def test_injected_allocation_failure_is_reported_and_recoverable(torch_cuda, monkeypatch):
+    """Host-side fault injection (DEM_FAULT=alloc): the allocation error comes back as
+    DEM_ERR_OOM and the same handle works once the fault is gone."""
+    sc = scenes.box_lattice(seed=3)
+    h = dem.dem_create(dem.config_from_params(sc.params))
+    try:
+        dem.dem_set_walls(h, sc.params.walls)
+        monkeypatch.setenv("DEM_FAULT", "alloc")
+        with pytest.raises(dem.DemError) as e:
+            dem.dem_set_particles(h, sc.x, sc.v, sc.w, sc.r)
+        assert e.value.status == 2 and "injected" in dem.dem_last_error(h)
+        monkeypatch.delenv("DEM_FAULT")
+        dem.dem_set_particles(h, sc.x, sc.v, sc.w, sc.r)
+        dem.dem_step(h, 5)
+    finally:
+        dem.dem_destroy(h)

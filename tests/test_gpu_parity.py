@@ -524,3 +524,32 @@ def test_list_mode_checkpoint_restore_bit_exact():
             dem.dem_destroy(h)
     assert np.array_equal(outs[0], outs[1])
     assert np.max(np.abs(outs[0] - xa)) <= 1e-9
+
+
+# ------------------------------------------------------------ statistics
+def test_settling_statistics_match_oracle():
+    """Loose random fill settling under gravity (the 262,144-sphere box's family, 3,000
+    spheres): FP32 mode against the FP64 oracle, kinetic energy at every 100th step and
+    the solid fraction of the bottom region at the end within 1%."""
+    sc = scenes.box_rsa(seed=12, n=3000)
+    p32 = sc.params.copy(precision="fp32")
+    ref = oracle.State(sc.params.copy(precision="fp64"), sc.x, sc.v, sc.w, sc.r)
+    ke_g, ke_o = [], []
+    with sim(p32, sc) as s:
+        for _ in range(10):
+            s.step(100)
+            ke_g.append(s.diagnostics()["ke_trans"])
+            ref.run(100, pair_mode="grid")
+            ke_o.append(oracle.diagnostics(ref.params, ref.x, ref.v, ref.w, ref.r)[0])
+        xg, _, _ = s.state()
+    ke_g, ke_o = np.array(ke_g), np.array(ke_o)
+    assert np.all(np.abs(ke_g - ke_o) <= 0.01 * ke_o)
+
+    def bottom_phi(x):
+        h = 20 * 1e-3
+        sel = x[:, 2] < h
+        vol = np.sum(4.0 / 3.0 * np.pi * sc.r[sel].astype(np.float64) ** 3)
+        lo, hi = sc.params.domain_lo, sc.params.domain_hi
+        return vol / ((hi[0] - lo[0]) * (hi[1] - lo[1]) * h)
+
+    assert bottom_phi(xg) == pytest.approx(bottom_phi(ref.x), rel=0.01)
