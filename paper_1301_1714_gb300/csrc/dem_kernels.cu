@@ -11,10 +11,15 @@
 
 #include "dem_domain.h"
 
-// Minimum resident 256-thread blocks per SM requested for the force kernel (caps its
-// registers at 65536 / (256 * value)).
+// Minimum resident 256-thread blocks per SM requested for the force kernel, which caps
+// its registers at 65536 / (256 * value): 80 registers in walk mode, 64 in list mode
+// (measured on GB300: the list-mode pass is 11% faster at 64 than at 80, the walk-mode
+// pass slightly slower).
 #ifndef DEM_FORCE_MIN_BLOCKS
 #define DEM_FORCE_MIN_BLOCKS 3
+#endif
+#ifndef DEM_FORCE_MIN_BLOCKS_LIST
+#define DEM_FORCE_MIN_BLOCKS_LIST 4
 #endif
 
 namespace demgb {
@@ -97,9 +102,33 @@ struct PF64 {
         prefetch_l1(&s.vx[j]);
         prefetch_l1(&s.wx[j]);
     }
+    struct Partner {
+        uint32_t j;
+        uint32_t id;
+        V3<double> v, w;
+    };
+    static __device__ __forceinline__ Partner load_partner(const State& s, uint32_t j) {
+        Partner o;
+        o.j = j;
+        o.id = __ldg(&s.id[j]);
+        load_vw(s, j, o.v, o.w);
+        return o;
+    }
+    static __device__ __forceinline__ void partner_vw(const Partner& o, V3<double>& v, V3<double>& w) {
+        v = o.v;
+        w = o.w;
+    }
+    static __device__ __forceinline__ bool exact_p(const State& s, const Partner& o, const Self& me,
+                                                   V3<double>& n, double& delta, float& rj) {
+        return exact_j(s, me, o.j, n, delta, rj);
+    }
     // Phase 2: geometry of a listed contact (the decision is the same as in scan_row).
     static __device__ __forceinline__ bool exact(const State& s, const Self& me, uint32_t j, const SceneDev&,
                                                  V3<double>& n, double& delta, float& rj) {
+        return exact_j(s, me, j, n, delta, rj);
+    }
+    static __device__ __forceinline__ bool exact_j(const State& s, const Self& me, uint32_t j, V3<double>& n,
+                                                   double& delta, float& rj) {
         const double dx = __dsub_rn(__ldg(&s.x[j]), me.x);
         const double dy = __dsub_rn(__ldg(&s.y[j]), me.y);
         const double dz = __dsub_rn(__ldg(&s.z[j]), me.z);
@@ -295,12 +324,36 @@ struct PF32 {
         prefetch_l1(&s.V[j]);
         prefetch_l1(&s.W[j]);
     }
+    // Everything phase 2 reads of a candidate, loaded together so the latencies overlap.
+    struct Partner {
+        float4 p0, p1, v, w;
+        uint32_t id;
+    };
+    static __device__ __forceinline__ Partner load_partner(const State& s, uint32_t j) {
+        Partner o;
+        o.p0 = __ldg(&s.P0[j]);
+        o.p1 = __ldg(&s.P1[j]);
+        o.v = __ldg(&s.V[j]);
+        o.w = __ldg(&s.W[j]);
+        o.id = __ldg(&s.id[j]);
+        return o;
+    }
+    static __device__ __forceinline__ void partner_vw(const Partner& o, V3<float>& v, V3<float>& w) {
+        v = mk(o.v.x, o.v.y, o.v.z);
+        w = mk(o.w.x, o.w.y, o.w.z);
+    }
+    static __device__ __forceinline__ bool exact_p(const State&, const Partner& o, const Self& me, V3<float>& n,
+                                                   float& delta, float& rj) {
+        return exact_xy(o.p0, o.p1, me, n, delta, rj);
+    }
     // Phase 2: the sign of R^2 - d^2 evaluated with error-free transformations (about
     // 2^-46 relative to R^2), then delta = (R^2 - d^2)/(R + d) and the unit normal.
     static __device__ __forceinline__ bool exact(const State& s, const Self& me, uint32_t j, const SceneDev&,
                                                  V3<float>& n, float& delta, float& rj) {
-        const float4 pj = __ldg(&s.P0[j]);
-        const float4 lj = __ldg(&s.P1[j]);
+        return exact_xy(__ldg(&s.P0[j]), __ldg(&s.P1[j]), me, n, delta, rj);
+    }
+    static __device__ __forceinline__ bool exact_xy(const float4 pj, const float4 lj, const Self& me, V3<float>& n,
+                                                    float& delta, float& rj) {
         float sx, tx, sy, ty, sz, tz;
         ff_diff(pj.x, lj.x, me.hx, me.lx, sx, tx);
         ff_diff(pj.y, lj.y, me.hy, me.ly, sy, ty);
@@ -523,7 +576,7 @@ __device__ __forceinline__ V3<T> find_spring(const uint32_t* s_oid, uint32_t bd,
 // decision, the law (Eq. 1 or Eqs. 2-10) and the springs; then walls, gravity, the
 // update (step 1) and the new cell key with its rank in the cell (step 2).
 template <class PR, int MODEL, bool EVAL, bool LIST>
-__global__ void __launch_bounds__(256, DEM_FORCE_MIN_BLOCKS) k_force(ForceArgs<PR> a) {
+__global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FORCE_MIN_BLOCKS) k_force(ForceArgs<PR> a) {
     using T = typename PR::T;
     extern __shared__ uint32_t smem[];
     const int cur = a.ctrl->cur;
@@ -633,10 +686,11 @@ __global__ void __launch_bounds__(256, DEM_FORCE_MIN_BLOCKS) k_force(ForceArgs<P
         V3<T> n;
         T delta;
         float rj;
-        if (!PR::exact(A, me, j, S, n, delta, rj)) continue;
-        const uint32_t gid = __ldg(&A.id[j]);
+        const typename PR::Partner o = PR::load_partner(A, j);
+        if (!PR::exact_p(A, o, me, n, delta, rj)) continue;
+        const uint32_t gid = o.id;
         V3<T> vj, wj;
-        PR::load_vw(A, j, vj, wj);
+        PR::partner_vw(o, vj, wj);
         const V3<T> v = me.v - vj;
         if (MODEL == 0) {
             const T rjT = (T)rj;
