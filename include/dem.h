@@ -52,6 +52,7 @@ enum { DEM_LINEAR = 0, DEM_HERTZ = 1 };       /* stiffness: constant k, or Eqs. 
 enum { DEM_FP64 = 0, DEM_FP32 = 1 };          /* precision mode, see dem_config */
 enum { DEM_HOST = 0, DEM_DEVICE = 1 };
 enum { DEM_PLANE = 0, DEM_CYLINDER_IN = 1 };
+enum { DEM_TERM_NO_ATTRACTION = 1, DEM_TERM_ROLLING = 2, DEM_TERM_ETA_T = 4, DEM_TERM_COHESION = 8 };
 
 /* Parameters of one scene (Sec. 3 "particle properties" and the grid of Sec. 4.1).
  *  model       DEM_PRACTICAL: F = F_t + F_n (Eq. 2), torque r_i n x F_t (Eq. 3),
@@ -83,6 +84,21 @@ enum { DEM_PLANE = 0, DEM_CYLINDER_IN = 1 };
  *              pass reads it instead of walking. K > 1 = as 0, and also at least every K
  *              steps. 0 and K > 1 need skin > 0; they find exactly the same contacts.
  *  block_size  threads per block of the force kernel (32..256); 0 = automatic (256)
+ *  terms       optional force terms added to Eqs. 2-10 (none is in the paper; its force
+ *              is built from separable terms so that terms can be added, Sec. 3), an OR of:
+ *              DEM_TERM_NO_ATTRACTION  the normal force never pulls: F_n = 0 when
+ *                                      F_n . n > 0 on i;
+ *              DEM_TERM_ROLLING        rolling resistance: torque -mu_roll R_eff |F_n|
+ *                                      w_rel/|w_rel| on i and its negative on j, w_rel =
+ *                                      w_i - w_j (or minus the wall's angular velocity);
+ *              DEM_TERM_ETA_T          eta_t = alpha_t sqrt(k_t m_eff) replaces eta in the
+ *                                      tangential part of Eq. 4;
+ *              DEM_TERM_COHESION       k_coh pi R_eff delta n on i, added after Eq. 5.
+ *              0 = the paper's law. Any nonzero value selects a separate compiled
+ *              variant of the force kernel; the paper's law runs without these terms.
+ *  mu_roll     rolling resistance coefficient (DEM_TERM_ROLLING)
+ *  alpha_t     tangential damping factor (DEM_TERM_ETA_T)
+ *  k_coh       cohesion energy density [N/m^2] (DEM_TERM_COHESION)
  *  max_contacts  per-particle capacity of the contact/history list (incl. walls);
  *              0 = 32; neighbour lists hold 2 x max_contacts. Exceeding either makes
  *              dem_step return DEM_ERR_CAPACITY.
@@ -99,6 +115,11 @@ typedef struct {
     double domain_lo[3], domain_hi[3];
     int32_t block_size;
     int32_t max_contacts;
+    int32_t terms;
+    int32_t pad;
+    double mu_roll;
+    double alpha_t;
+    double k_coh;
 } dem_config;
 
 /* A wall (Sec. 4.2 step 8): a body of infinite radius and mass.

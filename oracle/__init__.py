@@ -36,7 +36,8 @@ class _Params(ctypes.Structure):
                 ("cn", ctypes.c_double), ("ct", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("mu", ctypes.c_double), ("ksp", ctypes.c_double), ("kda", ctypes.c_double),
                 ("ksh", ctypes.c_double), ("origin", ctypes.c_double * 3), ("h", ctypes.c_double),
-                ("dims", ctypes.c_int64 * 3)]
+                ("dims", ctypes.c_int64 * 3), ("terms", ctypes.c_int32), ("pad2", ctypes.c_int32),
+                ("mu_roll", ctypes.c_double), ("alpha_t", ctypes.c_double), ("k_coh", ctypes.c_double)]
 
 
 class _Wall(ctypes.Structure):
@@ -106,6 +107,10 @@ def make_params(params) -> _Params:
     d = grid_dims(params)
     for a in range(3):
         c.dims[a] = d[a]
+    c.terms = int(getattr(params, "terms", 0))
+    c.mu_roll = float(getattr(params, "mu_roll", 0.0))
+    c.alpha_t = float(getattr(params, "alpha_t", 0.0))
+    c.k_coh = float(getattr(params, "k_coh", 0.0))
     return c
 
 

@@ -70,6 +70,11 @@ typedef struct {
     double ksp, kda, ksh;
     double origin[3], h;
     int64_t dims[3];
+    int32_t terms;      /* optional force terms (see law_practical) */
+    int32_t pad2;
+    double mu_roll;     /* rolling resistance coefficient (terms & 2) */
+    double alpha_t;     /* tangential damping factor (terms & 4) */
+    double k_coh;       /* cohesion energy density [N/m^2] (terms & 8) */
 } orc_params;
 
 typedef struct {
@@ -260,10 +265,21 @@ static vec3 hist_lookup(const hrec* h, int64_t nh, uint32_t i, uint32_t j) {
  * torque factor F_t (torques: T_i = r_i n x F_t, T_j = r_j n x F_t by Eq. 3), and the new
  * tangential spring. ri_wi and rj_wj are r omega of each body (for a wall, the partner's
  * term is folded into v via its surface velocity and rj_wj = 0). */
-typedef struct { vec3 F, Ft, dt_new; double overlap; } contact_out;
+typedef struct { vec3 F, Ft, dt_new, Mroll; double overlap; } contact_out;
 
+/* Optional terms beyond Eqs. 2-10 (the paper builds its force from separable terms so
+ * that terms can be added or removed, Sec. 3; none of these is in the paper):
+ *  terms & 1  the normal force never attracts: if F_n . n > 0 on i, F_n = 0 (the Coulomb
+ *             cap then uses |F_n| = 0);
+ *  terms & 2  rolling resistance: a torque -mu_roll R_eff |F_n| w_rel/|w_rel| on i (and
+ *             its negative on j), w_rel = w_i - w_j (a wall's angular velocity for walls);
+ *  terms & 4  a separate tangential damping coefficient eta_t = alpha_t sqrt(k_t m_eff)
+ *             in place of eta in the tangential part of Eq. 4 and in the spring reset;
+ *  terms & 8  cohesion: a force k_coh pi R_eff delta n on i (toward j; contact area of
+ *             a Hertzian contact, pi a^2 = pi R_eff delta) added after Eq. 5, so the
+ *             Coulomb cap and the rolling torque use the spring-dashpot |F_n| alone. */
 static contact_out law_practical(const orc_params* P, vec3 n, double delta, vec3 v, vec3 ri_wi, vec3 rj_wj,
-                                 double Reff, double meff, vec3 dt_old) {
+                                 double Reff, double meff, vec3 dt_old, vec3 wrel) {
     contact_out o;
     /* Eq. 6 */
     double vn_s = vdot(v, n);
@@ -283,18 +299,27 @@ static contact_out law_practical(const orc_params* P, vec3 n, double delta, vec3
     double eta = P->alpha * sqrt(kn * meff);
     /* Eq. 4 */
     vec3 Fn = vsub(vscale(n, -kn * delta), vscale(vn, eta));
-    vec3 Ft = vsub(vscale(dt, -kt), vscale(vt, eta));
+    if ((P->terms & 1) && vdot(Fn, n) > 0.0) Fn = v3(0.0, 0.0, 0.0);
+    double eta_t = eta;
+    if (P->terms & 4) eta_t = P->alpha_t * sqrt(kt * meff);
+    vec3 Ft = vsub(vscale(dt, -kt), vscale(vt, eta_t));
     /* Eq. 5 */
     double ftn = vnorm(Ft), fnn = vnorm(Fn);
     if (ftn > P->mu * fnn && ftn > 0.0) {
         Ft = vscale(Ft, P->mu * fnn / ftn);
-        if (kt > 0.0) dt = vscale(vadd(Ft, vscale(vt, eta)), -1.0 / kt);
+        if (kt > 0.0) dt = vscale(vadd(Ft, vscale(vt, eta_t)), -1.0 / kt);
     }
     /* Eq. 2 */
     o.F = vadd(Fn, Ft);
+    if (P->terms & 8) o.F = vadd(o.F, vscale(n, P->k_coh * ORC_PI * Reff * delta));
     o.Ft = Ft;
     o.dt_new = dt;
     o.overlap = delta;
+    o.Mroll = v3(0.0, 0.0, 0.0);
+    if (P->terms & 2) {
+        double wn = vnorm(wrel);
+        if (wn > 0.0) o.Mroll = vscale(wrel, -P->mu_roll * Reff * fnn / wn);
+    }
     return o;
 }
 
@@ -308,6 +333,7 @@ static contact_out law_simple(const orc_params* P, vec3 n, double delta, vec3 v)
     o.F = F;
     o.Ft = v3(0.0, 0.0, 0.0);
     o.dt_new = v3(0.0, 0.0, 0.0);
+    o.Mroll = v3(0.0, 0.0, 0.0);
     o.overlap = delta;
     return o;
 }
@@ -391,7 +417,8 @@ int64_t orc_forces(const orc_params* P, int32_t nwalls, const orc_wall* walls, i
             double Reff = 1.0 / (1.0 / ri + 1.0 / rj);
             double meff = 1.0 / (1.0 / mi + 1.0 / mj);
             vec3 dold = hist_lookup(hin, nh_in, i, j);
-            o = law_practical(P, n, delta, vrel, vscale(load3(w, i), ri), vscale(load3(w, j), rj), Reff, meff, dold);
+            o = law_practical(P, n, delta, vrel, vscale(load3(w, i), ri), vscale(load3(w, j), rj), Reff, meff, dold,
+                              vsub(load3(w, i), load3(w, j)));
             if (nout >= cap_out) { free(pairs); return -2; }
             hout[nout].i = i; hout[nout].j = j;
             hout[nout].d[0] = o.dt_new.x; hout[nout].d[1] = o.dt_new.y; hout[nout].d[2] = o.dt_new.z;
@@ -402,8 +429,8 @@ int64_t orc_forces(const orc_params* P, int32_t nwalls, const orc_wall* walls, i
         add3(F, i, o.F);
         add3(F, j, vscale(o.F, -1.0));
         vec3 tq = vcross(n, o.Ft);
-        add3(T, i, vscale(tq, ri));
-        add3(T, j, vscale(tq, rj));
+        add3(T, i, vadd(vscale(tq, ri), o.Mroll));
+        add3(T, j, vsub(vscale(tq, rj), o.Mroll));
         if (delta > maxov) maxov = delta;
         sumov += delta;
     }
@@ -419,7 +446,9 @@ int64_t orc_forces(const orc_params* P, int32_t nwalls, const orc_wall* walls, i
             uint32_t jw = ORC_WALL_BASE + (uint32_t)wi;
             if (P->model == 0) {
                 vec3 dold = hist_lookup(hin, nh_in, (uint32_t)i, jw);
-                o = law_practical(P, nn, delta, vrel, vscale(load3(w, i), ri), v3(0.0, 0.0, 0.0), ri, mi, dold);
+                vec3 wwall = v3(walls[wi].omega[0], walls[wi].omega[1], walls[wi].omega[2]);
+                o = law_practical(P, nn, delta, vrel, vscale(load3(w, i), ri), v3(0.0, 0.0, 0.0), ri, mi, dold,
+                                  vsub(load3(w, i), wwall));
                 if (nout >= cap_out) { free(pairs); return -2; }
                 hout[nout].i = (uint32_t)i; hout[nout].j = jw;
                 hout[nout].d[0] = o.dt_new.x; hout[nout].d[1] = o.dt_new.y; hout[nout].d[2] = o.dt_new.z;
@@ -428,7 +457,7 @@ int64_t orc_forces(const orc_params* P, int32_t nwalls, const orc_wall* walls, i
                 o = law_simple(P, nn, delta, vrel);
             }
             add3(F, i, o.F);
-            add3(T, i, vscale(vcross(nn, o.Ft), ri));
+            add3(T, i, vadd(vscale(vcross(nn, o.Ft), ri), o.Mroll));
             ++nwallc;
             if (delta > maxov) maxov = delta;
             sumov += delta;

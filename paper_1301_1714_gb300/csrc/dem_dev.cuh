@@ -40,7 +40,12 @@ struct SceneDev {
     double dt, g[3], kn, kt, cn, ct, alpha, mu, ksp, kda, ksh, cmass;   // cmass = rho*4/3*pi
     float dt_f, g_f[3], kn_f, kt_f, cn_f, ct_f, alpha_f, mu_f, ksp_f, kda_f, ksh_f, cmass_f;
     float eps_f;                // FP32 prefilter margin [m]
-    float pad2;
+    int32_t terms;              // optional force terms (DEM_TERM_*)
+    double mu_roll;             // rolling resistance coefficient
+    double alpha_t;             // tangential damping factor
+    double kcoh_pi;             // pi * cohesion energy density
+    float mu_roll_f, alpha_t_f, kcoh_pi_f;
+    float pad3;
     WallDev walls[DEM_MAX_WALLS];
 };
 
@@ -150,14 +155,17 @@ __device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
 // ----------------------------------------------------------- law parameters
 template <class T>
 struct Law {
-    T dt, kn, kt, cn, ct, alpha, mu, ksp, kda, ksh;
+    T dt, kn, kt, cn, ct, alpha, mu, ksp, kda, ksh, mu_roll, alpha_t, kcoh_pi;
     int stiffness;  // 0 linear, 1 Hertz
+    int terms;      // 1: no attractive normal force, 2: rolling resistance
 };
 __device__ __forceinline__ Law<double> law_of(const SceneDev& s, int stiffness, double) {
-    return Law<double>{s.dt, s.kn, s.kt, s.cn, s.ct, s.alpha, s.mu, s.ksp, s.kda, s.ksh, stiffness};
+    return Law<double>{s.dt,  s.kn,  s.kt,  s.cn,      s.ct,      s.alpha,   s.mu,
+                       s.ksp, s.kda, s.ksh, s.mu_roll, s.alpha_t, s.kcoh_pi, stiffness, s.terms};
 }
 __device__ __forceinline__ Law<float> law_of(const SceneDev& s, int stiffness, float) {
-    return Law<float>{s.dt_f, s.kn_f, s.kt_f, s.cn_f, s.ct_f, s.alpha_f, s.mu_f, s.ksp_f, s.kda_f, s.ksh_f, stiffness};
+    return Law<float>{s.dt_f,  s.kn_f,  s.kt_f,  s.cn_f,      s.ct_f,      s.alpha_f,   s.mu_f,
+                      s.ksp_f, s.kda_f, s.ksh_f, s.mu_roll_f, s.alpha_t_f, s.kcoh_pi_f, stiffness, s.terms};
 }
 
 // Practical contact law (Eqs. 2-10) for body i against partner j, seen from i:
@@ -167,9 +175,15 @@ __device__ __forceinline__ Law<float> law_of(const SceneDev& s, int stiffness, f
 //   dold   stored tangential spring from i's side (0 for a new contact)
 // Outputs: F (force on i, Eq. 2), Ft (tangential part after Eq. 5), dnew (Eq. 7 spring,
 // reset after a cap so that Eq. 4 holds).
-template <class T>
+// Optional terms, compiled in with TERMS and switched by P.terms: 1 = the normal force
+// never attracts (F_n = 0 when it would pull i toward j); 2 = rolling resistance, a torque
+// -mu_roll R_eff |F_n| w_rel/|w_rel| returned in Mroll (w_rel = w_i - w_j, or minus the
+// wall's angular velocity); 4 = eta_t = alpha_t sqrt(k_t m_eff) in the tangential part;
+// 8 = cohesion k_coh pi R_eff delta n added after the Coulomb cap.
+template <bool TERMS, class T>
 __device__ __forceinline__ void law_practical(const Law<T>& P, V3<T> n, T delta, V3<T> v, V3<T> rw, T Reff, T meff,
-                                              V3<T> dold, V3<T>& F, V3<T>& Ft, V3<T>& dnew) {
+                                              V3<T> dold, V3<T>& F, V3<T>& Ft, V3<T>& dnew, V3<T> wrel,
+                                              V3<T>& Mroll) {
     const T vn_s = dot(v, n);                                    // Eq. 6
     const V3<T> vn = n * vn_s;
     const V3<T> vt = (v - vn) + cross(rw, n);
@@ -183,20 +197,29 @@ __device__ __forceinline__ void law_practical(const Law<T>& P, V3<T> n, T delta,
         kt = P.ct * s;
     }
     const T eta = P.alpha * law_sqrt(kn * meff);                 // Eq. 10
-    const V3<T> Fn = n * (-kn * delta) - vn * eta;               // Eq. 4
-    V3<T> Ftt = dt * (-kt) - vt * eta;
+    V3<T> Fn = n * (-kn * delta) - vn * eta;                     // Eq. 4
+    if (TERMS && (P.terms & 1) && dot(Fn, n) > T(0)) Fn = mk(T(0), T(0), T(0));
+    T eta_t = eta;
+    if (TERMS && (P.terms & 4)) eta_t = P.alpha_t * law_sqrt(kt * meff);
+    V3<T> Ftt = dt * (-kt) - vt * eta_t;
     // Eq. 5, compared on squared lengths; the lengths are taken only when the cap applies
     const T ft2 = dot(Ftt, Ftt), fn2 = dot(Fn, Fn);
     if (ft2 > (P.mu * P.mu) * fn2 && ft2 > T(0)) {
         const T ftn = law_sqrt(ft2), fnn = law_sqrt(fn2);
         if (ftn > P.mu * fnn) {
             Ftt = Ftt * law_div(P.mu * fnn, ftn);
-            if (kt > T(0)) dt = (Ftt + vt * eta) * law_div(T(-1), kt);
+            if (kt > T(0)) dt = (Ftt + vt * eta_t) * law_div(T(-1), kt);
         }
     }
     F = Fn + Ftt;                                                // Eq. 2
+    if (TERMS && (P.terms & 8)) F = F + n * (P.kcoh_pi * Reff * delta);
     Ft = Ftt;
     dnew = dt;
+    Mroll = mk(T(0), T(0), T(0));
+    if (TERMS && (P.terms & 2)) {
+        const T wn2 = dot(wrel, wrel);
+        if (wn2 > T(0)) Mroll = wrel * law_div(-P.mu_roll * Reff * law_sqrt(fn2), law_sqrt(wn2));
+    }
 }
 
 // Simple law (Eq. 1): -k_sp delta n - k_da v - k_sh v_t, v_t = v - (v.n) n.

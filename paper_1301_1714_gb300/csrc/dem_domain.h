@@ -22,6 +22,7 @@ struct Domain {
     // configuration
     int precision = 0;   // 0 FP64, 1 FP32 (compensated positions)
     int model = 0;       // 0 practical, 1 simple
+    int terms = 0;       // union of the scenes' optional force terms (selects the kernel variant)
     int stiffness = 0;   // 0 linear, 1 Hertz
     int maxc = 32;       // history slots per particle
     int block = 128;     // force kernel block size

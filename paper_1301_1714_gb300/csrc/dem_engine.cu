@@ -160,6 +160,13 @@ void fill_scene(dem_handle* h, SceneDev& S, uint32_t p0, uint32_t np, uint32_t c
     S.dt_f = (float)c.dt; S.kn_f = (float)c.kn; S.kt_f = (float)c.kt; S.cn_f = (float)c.cn; S.ct_f = (float)c.ct;
     S.alpha_f = (float)c.alpha; S.mu_f = (float)c.mu; S.ksp_f = (float)c.ksp; S.kda_f = (float)c.kda;
     S.ksh_f = (float)c.ksh; S.cmass_f = (float)S.cmass;
+    S.terms = c.terms;
+    S.mu_roll = c.mu_roll;
+    S.mu_roll_f = (float)c.mu_roll;
+    S.alpha_t = c.alpha_t;
+    S.alpha_t_f = (float)c.alpha_t;
+    S.kcoh_pi = c.k_coh * 3.14159265358979323846;
+    S.kcoh_pi_f = (float)S.kcoh_pi;
     // FP32 prefilter margin: bounds the FP32 error of |hi_j - hi_i| for coordinates up to X
     double X = 0.0;
     for (int a = 0; a < 3; ++a) {
@@ -196,6 +203,13 @@ dem_status validate_config(const dem_config* c, std::string& why) {
         return DEM_ERR_INVALID_ARG;
     }
     if (c->max_contacts < 0 || c->max_contacts > 64) { why = "max_contacts must be in [0, 64]"; return DEM_ERR_INVALID_ARG; }
+    if (c->terms & ~(DEM_TERM_NO_ATTRACTION | DEM_TERM_ROLLING | DEM_TERM_ETA_T | DEM_TERM_COHESION)) {
+        why = "unknown terms";
+        return DEM_ERR_INVALID_ARG;
+    }
+    if (c->terms && c->model != DEM_PRACTICAL) { why = "optional terms need the practical model"; return DEM_ERR_INVALID_ARG; }
+    for (double q : {c->mu_roll, c->alpha_t, c->k_coh})
+        if (!(q >= 0.0) || !std::isfinite(q)) { why = "mu_roll, alpha_t and k_coh must be finite and >= 0"; return DEM_ERR_INVALID_ARG; }
     return DEM_OK;
 }
 
@@ -491,6 +505,7 @@ dem_status dem_create(const dem_config* cfg, int device, void* cuda_stream, dem_
     Domain& d = h->d;
     d.precision = cfg->precision;
     d.model = cfg->model;
+    d.terms = cfg->terms;
     d.stiffness = cfg->stiffness;
     d.maxc = cfg->max_contacts > 0 ? cfg->max_contacts : 32;
     d.block = cfg->block_size > 0 ? cfg->block_size : 256;
@@ -1031,6 +1046,9 @@ dem_status repack(dem_batch* b) {
     Domain nd;
     nd.precision = od.precision;
     nd.model = od.model;
+    nd.terms = 0;
+    for (BatchScene* sc : kept) nd.terms |= sc->cfg.terms;
+    for (BatchScene* sc : fresh) nd.terms |= sc->cfg.terms;
     nd.stiffness = od.stiffness;
     nd.maxc = od.maxc;
     nd.maxn = od.maxn;

@@ -170,6 +170,9 @@ struct PF64 {
         cp = a * ax + n * W.radius;
         return true;
     }
+    static __device__ __forceinline__ V3<double> wall_omega(const WallDev& W) {
+        return mk(W.omega[0], W.omega[1], W.omega[2]);
+    }
     static __device__ __forceinline__ V3<double> wall_vel(const WallDev& W, V3<double> cp) {
         return mk(W.vel[0], W.vel[1], W.vel[2]) + cross(mk(W.omega[0], W.omega[1], W.omega[2]), cp);
     }
@@ -475,6 +478,9 @@ struct PF32 {
         cp = mk(cpp[0], cpp[1], cpp[2]);
         return true;
     }
+    static __device__ __forceinline__ V3<float> wall_omega(const WallDev& W) {
+        return mk(W.omegaf[0], W.omegaf[1], W.omegaf[2]);
+    }
     static __device__ __forceinline__ V3<float> wall_vel(const WallDev& W, V3<float> cp) {
         return mk(W.velf[0], W.velf[1], W.velf[2]) + cross(mk(W.omegaf[0], W.omegaf[1], W.omegaf[2]), cp);
     }
@@ -575,9 +581,13 @@ __device__ __forceinline__ V3<T> find_spring(const uint32_t* s_oid, uint32_t bd,
 // iterates max-list-length times instead of once per candidate), taking the contact
 // decision, the law (Eq. 1 or Eqs. 2-10) and the springs; then walls, gravity, the
 // update (step 1) and the new cell key with its rank in the cell (step 2).
+// MODEL: 0 the practical law, 1 the simple law (Eq. 1), 2 the practical law with the
+// scene's optional terms (no attraction, rolling resistance).
 template <class PR, int MODEL, bool EVAL, bool LIST>
 __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FORCE_MIN_BLOCKS) k_force(ForceArgs<PR> a) {
     using T = typename PR::T;
+    constexpr bool PRACT = MODEL != 1;
+    constexpr bool TERMS = MODEL == 2;
     extern __shared__ uint32_t smem[];
     const int cur = a.ctrl->cur;
     const typename PR::State A = cur ? a.S1 : a.S0;
@@ -603,7 +613,7 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
     if (valid) {
         me = PR::load(A, q);
         src = pv ? a.perm[q] : q;
-        if (MODEL == 0 || !S.active) {
+        if (PRACT || !S.active) {
             cnt_old = min(a.hin_cnt[src], maxc);
             // the stored springs are streamed from DRAM: start their loads now so they are
             // in L1 when phase 2 matches contacts against them
@@ -692,7 +702,7 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
         V3<T> vj, wj;
         PR::partner_vw(o, vj, wj);
         const V3<T> v = me.v - vj;
-        if (MODEL == 0) {
+        if (PRACT) {
             const T rjT = (T)rj;
             const V3<T> rw = mk(sym_madd(ri, me.w.x, rjT, wj.x), sym_madd(ri, me.w.y, rjT, wj.y),
                                 sym_madd(ri, me.w.z, rjT, wj.z));
@@ -700,10 +710,11 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
             const T meff = law_div(mi * mj, mi + mj);
             const T Reff = law_div(ri * rjT, ri + rjT);
             const V3<T> dold = find_spring(s_oid, bd, tid, cnt_old, gid, a.hin_d, (size_t)maxc, cap, src);
-            V3<T> Fc, Ftc, dnew;
-            law_practical(L, n, delta, v, rw, Reff, meff, dold, Fc, Ftc, dnew);
+            V3<T> Fc, Ftc, dnew, Mr;
+            law_practical<TERMS>(L, n, delta, v, rw, Reff, meff, dold, Fc, Ftc, dnew, me.w - wj, Mr);
             F = F + Fc;
             Tq = Tq + cross(n, Ftc) * ri;
+            if (TERMS) Tq = Tq + Mr;
             if (nnew < maxc) {
                 a.hout_pid[nnew * cap + q] = gid;
                 a.hout_d[(0 * (size_t)maxc + nnew) * cap + q] = dnew.x;
@@ -727,13 +738,14 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
             if (!PR::wall(W, me, S, n, delta, cp)) continue;
             const V3<T> v = me.v - PR::wall_vel(W, cp);
             const uint32_t gid = DEM_WALL_BASE + (uint32_t)w;
-            if (MODEL == 0) {
+            if (PRACT) {
                 const V3<T> rw = me.w * ri;
                 const V3<T> dold = find_spring(s_oid, bd, tid, cnt_old, gid, a.hin_d, (size_t)maxc, cap, src);
-                V3<T> Fc, Ftc, dnew;
-                law_practical(L, n, delta, v, rw, ri, mi, dold, Fc, Ftc, dnew);
+                V3<T> Fc, Ftc, dnew, Mr;
+                law_practical<TERMS>(L, n, delta, v, rw, ri, mi, dold, Fc, Ftc, dnew, me.w - PR::wall_omega(W), Mr);
                 F = F + Fc;
                 Tq = Tq + cross(n, Ftc) * ri;
+                if (TERMS) Tq = Tq + Mr;
                 if (nnew < maxc) {
                     a.hout_pid[nnew * cap + q] = gid;
                     a.hout_d[(0 * (size_t)maxc + nnew) * cap + q] = dnew.x;
@@ -750,7 +762,7 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
         }
         if (nnew > maxc) raise_status(a.st, ST_CAPACITY, (int32_t)q);
         c_nnew = nnew;
-        if (MODEL == 0 || EVAL) a.hout_cnt[q] = min(nnew, maxc);
+        if (PRACT || EVAL) a.hout_cnt[q] = min(nnew, maxc);
         // gravity, once per particle
         {
             const T gx = sizeof(T) == 8 ? (T)S.g[0] : (T)S.g_f[0];
@@ -1310,11 +1322,14 @@ static cudaError_t force_impl(Domain& d, const typename PR::State& S0, const typ
         return cudaSuccess;
     };
     cudaError_t e;
+    const int model = d.model != 0 ? 1 : (d.terms != 0 ? 2 : 0);
     if (d.list_mode) {
-        if (d.model == 0) e = eval ? launch(k_force<PR, 0, true, true>) : launch(k_force<PR, 0, false, true>);
+        if (model == 0) e = eval ? launch(k_force<PR, 0, true, true>) : launch(k_force<PR, 0, false, true>);
+        else if (model == 2) e = eval ? launch(k_force<PR, 2, true, true>) : launch(k_force<PR, 2, false, true>);
         else e = eval ? launch(k_force<PR, 1, true, true>) : launch(k_force<PR, 1, false, true>);
     } else {
-        if (d.model == 0) e = eval ? launch(k_force<PR, 0, true, false>) : launch(k_force<PR, 0, false, false>);
+        if (model == 0) e = eval ? launch(k_force<PR, 0, true, false>) : launch(k_force<PR, 0, false, false>);
+        else if (model == 2) e = eval ? launch(k_force<PR, 2, true, false>) : launch(k_force<PR, 2, false, false>);
         else e = eval ? launch(k_force<PR, 1, true, false>) : launch(k_force<PR, 1, false, false>);
     }
     if (e != cudaSuccess) return e;

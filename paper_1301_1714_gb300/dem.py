@@ -22,6 +22,7 @@ DEM_LINEAR, DEM_HERTZ = 0, 1
 DEM_FP64, DEM_FP32 = 0, 1
 DEM_HOST, DEM_DEVICE = 0, 1
 DEM_PLANE, DEM_CYLINDER_IN = 0, 1
+DEM_TERM_NO_ATTRACTION, DEM_TERM_ROLLING, DEM_TERM_ETA_T, DEM_TERM_COHESION = 1, 2, 4, 8
 WALL_BASE = 0xFFFFFF00
 
 _D3 = ctypes.c_double * 3
@@ -34,7 +35,9 @@ class dem_config(ctypes.Structure):
                 ("ct", ctypes.c_double), ("alpha", ctypes.c_double), ("mu", ctypes.c_double),
                 ("ksp", ctypes.c_double), ("kda", ctypes.c_double), ("ksh", ctypes.c_double),
                 ("skin", ctypes.c_double), ("cell_size", ctypes.c_double), ("domain_lo", _D3), ("domain_hi", _D3),
-                ("block_size", ctypes.c_int32), ("max_contacts", ctypes.c_int32)]
+                ("block_size", ctypes.c_int32), ("max_contacts", ctypes.c_int32), ("terms", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("mu_roll", ctypes.c_double), ("alpha_t", ctypes.c_double),
+                ("k_coh", ctypes.c_double)]
 
 
 class dem_wall(ctypes.Structure):
@@ -165,6 +168,10 @@ def config_from_params(p, block_size=0, max_contacts=0) -> dem_config:
     c.cell_size = p.cell_size
     c.block_size = block_size
     c.max_contacts = max_contacts
+    c.terms = int(getattr(p, "terms", 0))
+    c.mu_roll = float(getattr(p, "mu_roll", 0.0))
+    c.alpha_t = float(getattr(p, "alpha_t", 0.0))
+    c.k_coh = float(getattr(p, "k_coh", 0.0))
     return c
 
 

@@ -192,6 +192,10 @@ class Params:
     domain_lo: tuple = (0.0, 0.0, 0.0)
     domain_hi: tuple = (1.0, 1.0, 1.0)
     resort_interval: int = 1
+    terms: int = 0                   # optional terms: 1 no attraction, 2 rolling, 4 eta_t, 8 cohesion
+    mu_roll: float = 0.0             # rolling resistance coefficient
+    alpha_t: float = 0.0             # tangential damping factor (terms & 4)
+    k_coh: float = 0.0               # cohesion energy density [N/m^2] (terms & 8)
     walls: list = field(default_factory=list)
 
     def copy(self, **kw):
