@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--serve-nmax", type=int, default=131072)
     ap.add_argument("--serve-steps", type=str, default="500,2000", help="step budget range of the requests")
     ap.add_argument("--serve-hbm-gb", type=float, default=16.0)
+    ap.add_argument("--hopper-steps", type=int, default=2000,
+                    help="timed steps of the hopper comparison (the paper's own benchmark shape; 0 = skip)")
+    ap.add_argument("--hopper-settle", type=int, default=3000, help="fill steps (closed bottom) before the slit opens")
+    ap.add_argument("--hopper-drain", type=int, default=20000, help="steps after the slit opens, before timing")
     return ap.parse_args()
 
 
@@ -160,6 +164,63 @@ def run_batch_bench(args, dem, dev_index, stream):
             "sequential_sample": f"first {min(args.batch_seq_scenes, len(mix))} scenes, one handle each, "
                                  f"{args.batch_steps} steps",
             "batched_over_sequential": round(batched / seq, 2) if seq else None}
+
+
+def run_hopper_bench(args, dem, dev_index, stream):
+    """The paper's benchmark shape (Sec. 5, Table 3): 131,072 equal spheres in a box drain
+    through a slit in its bottom onto a floor. The box is filled at rest with the bottom
+    closed (accelerated settling), the slit opens, the flow runs `hopper_drain` steps, then
+    the practical and the simple model are each timed for `hopper_steps` steps from that
+    state (FP32, skin-driven sorting), and the FP64 oracle on a bounded slab of it."""
+    import torch
+    from paper_1301_1714_gb300 import scenes
+    closed = scenes.hopper(seed=args.seed, open_slit=False)
+    opened = scenes.hopper(seed=args.seed, open_slit=True)
+    N = closed.n
+    x, v, w = settle_bed(dem, closed, dev_index, stream.cuda_stream, args.hopper_settle, 0)
+    rmax = float(closed.r.max())
+    skin = args.skin_r * rmax
+    out = {"workload": f"hopper: {N:,} equal spheres r=1 mm, box 134.4 x 67.2 mm filled at rest, slit 12 mm wide "
+                       f"across x opened, {args.hopper_drain} steps of flow, then timed",
+           "n_particles": N, "steps": args.hopper_steps}
+    for model in ("practical", "simple"):
+        p = opened.params.copy(model=model, resort_interval=0, skin=skin, cell_size=opened.params.cell_size + skin)
+        h = dem.dem_create(dem.config_from_params(p), dev_index, stream.cuda_stream)
+        try:
+            dem.dem_set_walls(h, p.walls)
+            dem.dem_set_particles(h, x, v, w, closed.r)
+            if model == "practical":
+                dem.dem_step(h, args.hopper_drain)
+                xd, vd, wd = dem.dem_get_state(h, N)
+                zp = opened.params.walls[6]["p"][2]
+                out["below_plate_at_start"] = int(np.count_nonzero(xd[:, 2] < zp))
+            else:
+                dem.dem_set_particles(h, xd, vd, wd, closed.r)
+            dem.dem_step(h, 50)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            dem.dem_step(h, args.hopper_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            d = dict(zip(dem.DIAG_NAMES, dem.dem_get_diagnostics(h)))
+            out[model] = {"value": round(N * args.hopper_steps / (ms / 1e3), 1), "unit": UNIT,
+                          "ms_per_step": round(ms / args.hopper_steps, 4),
+                          "pair_contacts": d["pair_contacts"], "wall_contacts": d["wall_contacts"]}
+        finally:
+            dem.dem_destroy(h)
+    out["practical_over_simple_slowdown"] = round(out["simple"]["value"] / out["practical"]["value"], 3)
+    if not args.no_cpu_baseline:
+        state = scenes.Scene("hopper_flow", xd, vd, wd, closed.r, opened.params)
+        val, desc, _, _ = oracle_sample(args, state, 0.5 * args.cpu_seconds, state="the draining hopper")
+        out["cpu_oracle"] = {"value": round(val, 1), "unit": UNIT, "cores": 1, "sample": desc}
+        out["gpu_practical_over_cpu"] = round(out["practical"]["value"] / val, 1)
+    out["paper_table3_context"] = {"unit": "particles/s", "practical_gpu_opencl_c2050": 2.96e6,
+                                   "simple_gpu_cuda_c2050": 2.2359e7, "practical_cpu_x5670_1core": 4.74e5,
+                                   "note": "another machine and an unstated geometry: context, not a target"}
+    return out
 
 
 def run_serve_bench(args, dem, dev_index, stream):
@@ -273,7 +334,7 @@ def profiled_traffic_per_particle(list_mode=False):
 
 
 # ------------------------------------------------------------------ oracle sample
-def oracle_sample(args, sc, target_s, max_steps=None):
+def oracle_sample(args, sc, target_s, max_steps=None, state="the same seeded workload before settling"):
     """Time the FP64 oracle on a slab of the workload (particles with x below a cut),
     sized so that the steps take about target_s seconds. Returns (value, sample text,
     steps, seconds)."""
@@ -294,8 +355,8 @@ def oracle_sample(args, sc, target_s, max_steps=None):
     dt = time.perf_counter() - t0
     value = n_s * steps / dt
     xcut = float(sc.x[sel, 0].max())
-    desc = (f"FP64 oracle (C, 1 thread), {steps} step(s) of the {n_s:,} spheres with x <= {xcut:.4f} m of the same "
-            f"seeded workload before settling (grid pair search), {dt:.1f} s")
+    desc = (f"FP64 oracle (C, 1 thread), {steps} step(s) of the {n_s:,} spheres with x <= {xcut:.4f} m of "
+            f"{state} (grid pair search), {dt:.1f} s")
     return value, desc, steps, dt
 
 
@@ -475,6 +536,8 @@ def run_ours(args):
 
         batch = run_batch_bench(args, dem, dev.index, stream) if args.batch_scenes > 0 else None
         serving = run_serve_bench(args, dem, dev.index, stream) if args.serve_requests > 0 else None
+        hopper = (run_hopper_bench(args, dem, dev.index, stream)
+                  if args.hopper_steps > 0 and rank == 0 and world == 1 else None)
         out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -485,7 +548,7 @@ def run_ours(args):
                           "l2": "inputs larger than L2 (no flush needed)",
                           "device_bytes": dem.dem_device_bytes(h), "parallelism": f"replicas x{world}"},
                "roofline": roof, "gpu_launches": int(launches), "clocks": clocks, "simple": simple, "e2e": e2e,
-               "batch": batch, "serving": serving, "autotune": tuned, "sort_every_step": every,
+               "batch": batch, "serving": serving, "hopper": hopper, "autotune": tuned, "sort_every_step": every,
                "diagnostics": {k: diag[k] for k in ("pair_contacts", "wall_contacts", "max_overlap", "ke_trans")}}
     finally:
         dem.dem_destroy(h)

@@ -51,7 +51,7 @@ enum { DEM_PRACTICAL = 0, DEM_SIMPLE = 1 };   /* contact model: Eqs. 2-10 or Eq.
 enum { DEM_LINEAR = 0, DEM_HERTZ = 1 };       /* stiffness: constant k, or Eqs. 8-9 */
 enum { DEM_FP64 = 0, DEM_FP32 = 1 };          /* precision mode, see dem_config */
 enum { DEM_HOST = 0, DEM_DEVICE = 1 };
-enum { DEM_PLANE = 0, DEM_CYLINDER_IN = 1 };
+enum { DEM_PLANE = 0, DEM_CYLINDER_IN = 1, DEM_HALF_PLATE = 2 };
 enum { DEM_TERM_NO_ATTRACTION = 1, DEM_TERM_ROLLING = 2, DEM_TERM_ETA_T = 4, DEM_TERM_COHESION = 8 };
 
 /* Parameters of one scene (Sec. 3 "particle properties" and the grid of Sec. 4.1).
@@ -129,6 +129,15 @@ typedef struct {
  *                   p along the unit vector n (in DEM_FP32 mode n must be a coordinate
  *                   axis); a sphere touches it when its centre is farther than
  *                   radius - r from the axis.
+ *  DEM_HALF_PLATE   a plate of zero thickness: the half-plane through p with unit normal
+ *                   n on the side (y - p) . u >= 0 of its edge line (the line through p
+ *                   along n x u; u a unit vector orthogonal to n). Touched from either
+ *                   side: a sphere touches the nearest plate point (the projection of its
+ *                   centre, or the edge point beside it when the projection falls off the
+ *                   plate) when that point is closer than r. Two half-plates with opposite
+ *                   u make a plate with a slit: the paper's benchmark drains a box through
+ *                   a slit in its bottom onto a floor (Sec. 5; the geometry is not given).
+ *                   In DEM_FP32 mode n and u must be coordinate axes. radius is unused.
  *  omega, vel       the wall surface moves with velocity vel + omega x (c - p) at a
  *                   point c; this velocity replaces the partner's in Eq. 6.
  */
@@ -138,6 +147,7 @@ typedef struct {
     double p[3], n[3];
     double radius;
     double omega[3], vel[3];
+    double u[3];
 } dem_wall;
 
 typedef struct dem_handle dem_handle;
@@ -161,6 +171,16 @@ dem_status dem_set_walls(dem_handle* h, int nwalls, const dem_wall* walls);
  * device during these steps (DEM_ERR_CAPACITY, DEM_ERR_NONFINITE), after which the state
  * is the one reached when the error was detected at the end of the call. */
 dem_status dem_step(dem_handle* h, int64_t nsteps);
+
+/* Runs until the particles come to rest: the paper continues its benchmark until every
+ * particle moves less than a set amount (Sec. 5). Steps in chunks of check_every (>= 1)
+ * through dem_step; after each chunk reads the largest displacement of any particle in
+ * the chunk's last step, max |v'| dt (FP32 in DEM_FP32 mode), and stops when it is below
+ * disp_threshold or when max_steps (>= 0) steps have run. Outputs (any may be NULL):
+ * steps_done, last_max_disp (the displacement read after the last chunk, 0 when no step
+ * ran) and settled (1 if the threshold was met). Errors as dem_step. */
+dem_status dem_run_until(dem_handle* h, int64_t max_steps, double disp_threshold, int64_t check_every,
+                         int64_t* steps_done, double* last_max_disp, int* settled);
 
 /* Copies the current state out in id order (any pointer may be NULL to skip it). */
 dem_status dem_get_state(dem_handle* h, double* x, double* v, double* w, int where);

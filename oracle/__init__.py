@@ -43,7 +43,7 @@ class _Params(ctypes.Structure):
 class _Wall(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("pad", ctypes.c_int32), ("p", ctypes.c_double * 3),
                 ("n", ctypes.c_double * 3), ("radius", ctypes.c_double), ("omega", ctypes.c_double * 3),
-                ("vel", ctypes.c_double * 3)]
+                ("vel", ctypes.c_double * 3), ("u", ctypes.c_double * 3)]
 
 
 def build(force: bool = False) -> str:
@@ -78,12 +78,21 @@ def _L():
         lib.orc_run.restype = ctypes.c_int
         lib.orc_diagnostics.argtypes = [P, I64, P, P, P, P, P]
         lib.orc_diagnostics.restype = None
+        lib.orc_struct_sizes.argtypes = [P]
+        lib.orc_struct_sizes.restype = None
         _lib = lib
     return _lib
 
 
 def _ptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def struct_sizes_match():
+    """True if the C records have the sizes of their ctypes mirrors."""
+    out = np.zeros(2, dtype=np.int64)
+    _L().orc_struct_sizes(_ptr(out))
+    return int(out[0]) == ctypes.sizeof(_Params) and int(out[1]) == ctypes.sizeof(_Wall)
 
 
 def grid_dims(params):
@@ -117,10 +126,11 @@ def make_params(params) -> _Params:
 def make_walls(walls):
     arr = (_Wall * max(1, len(walls)))()
     for k, w in enumerate(walls):
-        arr[k].kind = {"plane": 0, "cylinder": 1}[w["kind"]]
+        arr[k].kind = {"plane": 0, "cylinder": 1, "half_plate": 2}[w["kind"]]
         for a in range(3):
             arr[k].p[a] = w["p"][a]
             arr[k].n[a] = w["n"][a]
+            arr[k].u[a] = w.get("u", (0, 0, 0))[a]
             arr[k].omega[a] = w.get("omega", (0, 0, 0))[a]
             arr[k].vel[a] = w.get("vel", (0, 0, 0))[a]
         arr[k].radius = w.get("radius", 0.0)

@@ -78,10 +78,18 @@ typedef struct {
 } orc_params;
 
 typedef struct {
-    int32_t kind;       /* 0 plane (n = unit normal into the domain), 1 cylinder interior (n = unit axis) */
+    int32_t kind;       /* 0 plane (n = unit normal into the domain), 1 cylinder interior (n = unit axis),
+                           2 half-plate: zero-thickness half-plane through p with unit normal n,
+                           covering the side (y - p).u >= 0 of its edge (u unit, in the plane) */
     int32_t pad;
-    double p[3], n[3], radius, omega[3], vel[3];
+    double p[3], n[3], radius, omega[3], vel[3], u[3];
 } orc_wall;
+
+/* Sizes of the parameter and wall records (checked against the Python mirrors). */
+void orc_struct_sizes(int64_t* out) {
+    out[0] = (int64_t)sizeof(orc_params);
+    out[1] = (int64_t)sizeof(orc_wall);
+}
 
 /* ------------------------------------------------------------- 3-vectors */
 typedef struct { double x, y, z; } vec3;
@@ -351,6 +359,25 @@ static int wall_geometry(const orc_wall* W, vec3 x, double r, vec3* n, double* d
         *n = vscale(a, -1.0);
         *delta = d;
         *c = vsub(x, vscale(a, s));
+        return 1;
+    } else if (W->kind == 2) {
+        /* Half-plate (two of them with opposite u make a slit, the bottom of the paper's
+         * benchmark box, Sec. 5): touched from either side. The nearest plate point to
+         * the centre is its projection when that lies on the plate (s >= 0), else the
+         * point of the edge line (s = 0) beside it. */
+        vec3 u = v3(W->u[0], W->u[1], W->u[2]);
+        vec3 q = vsub(x, p);
+        double h = vdot(q, a);                  /* height above the plate's plane */
+        double s = vdot(q, u);                  /* distance from the edge line into the plate */
+        vec3 e = vscale(a, -h);                 /* from the centre to the nearest plate point */
+        if (s < 0.0) e = vadd(e, vscale(u, -s));
+        double dist = vnorm(e);
+        double d = r - dist;
+        if (!(d > 0.0)) return 0;
+        if (dist > 0.0) *n = vscale(e, 1.0 / dist);
+        else *n = vscale(a, -1.0);
+        *delta = d;
+        *c = vadd(x, e);
         return 1;
     } else {
         vec3 q = vsub(x, p);

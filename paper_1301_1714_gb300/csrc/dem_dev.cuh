@@ -19,9 +19,12 @@ namespace demgb {
 
 // ------------------------------------------------------------------ scene table
 struct WallDev {
-    int32_t kind;       // 0 plane, 1 cylinder interior
-    int32_t axis;       // cylinder axis index when it is a coordinate axis, else -1
-    double p[3], n[3], radius, omega[3], vel[3];
+    int32_t kind;       // 0 plane, 1 cylinder interior, 2 half-plate
+    int32_t axis;       // cylinder axis / plane or plate normal index when it is a coordinate axis, else -1
+    int32_t uaxis;      // half-plate: index of u when it is a coordinate axis, else -1
+    int32_t pad;
+    double p[3], n[3], radius, omega[3], vel[3], u[3];
+    float uf[3];
     float p_hi[3], p_lo[3];     // p split into hi + lo (FP32 mode)
     float n_hi[3], n_lo[3];     // n split into hi + lo
     float rad_hi, rad_lo;       // radius split
@@ -56,7 +59,8 @@ struct CountersDev {
     uint32_t max_overlap_bits;   // bits of the largest overlap as a non-negative float
     uint32_t clamped;            // particles whose new cell index was clamped to the grid
     uint32_t max_nnew;           // largest per-particle contact count
-    uint32_t pad[3];
+    uint32_t max_disp2_bits;     // bits of the largest squared displacement of the step (|v'| dt)^2
+    uint32_t pad[2];
 };
 // Status word: the first error raised on the device (sticky until the host reads it).
 struct StatusDev {

@@ -128,12 +128,49 @@ WallDev make_wall(const dem_wall& w) {
     }
     W.radius = w.radius;
     split_f(w.radius, W.rad_hi, W.rad_lo);
-    // coordinate-axis normal / axis
+    W.uaxis = -1;
+    for (int a = 0; a < 3; ++a) {
+        W.u[a] = w.u[a];
+        W.uf[a] = (float)w.u[a];
+    }
+    // coordinate-axis normal / axis (and the plate's axis across the slit)
     for (int a = 0; a < 3; ++a) {
         const int b = (a + 1) % 3, c = (a + 2) % 3;
         if (std::fabs(w.n[a]) == 1.0 && w.n[b] == 0.0 && w.n[c] == 0.0) W.axis = a;
+        if (w.kind == DEM_HALF_PLATE && std::fabs(w.u[a]) == 1.0 && w.u[b] == 0.0 && w.u[c] == 0.0) W.uaxis = a;
     }
     return W;
+}
+
+bool check_wall(const dem_wall& w, int precision, std::string& why) {
+    if (w.kind != DEM_PLANE && w.kind != DEM_CYLINDER_IN && w.kind != DEM_HALF_PLATE) { why = "wall kind"; return false; }
+    if (!finite3(w.p) || !finite3(w.n) || !finite3(w.omega) || !finite3(w.vel) || !finite3(w.u)) {
+        why = "wall vectors must be finite";
+        return false;
+    }
+    const double nn = w.n[0] * w.n[0] + w.n[1] * w.n[1] + w.n[2] * w.n[2];
+    if (std::fabs(nn - 1.0) > 1e-12) { why = "wall n must be a unit vector"; return false; }
+    if (w.kind == DEM_CYLINDER_IN) {
+        if (!(w.radius > 0.0) || !std::isfinite(w.radius)) { why = "cylinder radius must be > 0"; return false; }
+        if (precision == DEM_FP32 && make_wall(w).axis < 0) {
+            why = "in DEM_FP32 mode a cylinder axis must be a coordinate axis";
+            return false;
+        }
+    }
+    if (w.kind == DEM_HALF_PLATE) {
+        const double uu = w.u[0] * w.u[0] + w.u[1] * w.u[1] + w.u[2] * w.u[2];
+        const double un = w.u[0] * w.n[0] + w.u[1] * w.n[1] + w.u[2] * w.n[2];
+        if (std::fabs(uu - 1.0) > 1e-12 || std::fabs(un) > 1e-12) {
+            why = "half-plate u must be a unit vector orthogonal to n";
+            return false;
+        }
+        const WallDev W = make_wall(w);
+        if (precision == DEM_FP32 && (W.axis < 0 || W.uaxis < 0)) {
+            why = "in DEM_FP32 mode a half-plate's n and u must be coordinate axes";
+            return false;
+        }
+    }
+    return true;
 }
 
 void fill_scene(dem_handle* h, SceneDev& S, uint32_t p0, uint32_t np, uint32_t c0) {
@@ -547,17 +584,8 @@ dem_status dem_set_walls(dem_handle* h, int nwalls, const dem_wall* walls) {
     if (nwalls < 0 || nwalls > DEM_MAX_WALLS || (nwalls > 0 && !walls))
         return fail(h, DEM_ERR_INVALID_ARG, "nwalls must be in [0, 8]");
     for (int k = 0; k < nwalls; ++k) {
-        const dem_wall& w = walls[k];
-        if (w.kind != DEM_PLANE && w.kind != DEM_CYLINDER_IN) return fail(h, DEM_ERR_INVALID_ARG, "wall kind");
-        if (!finite3(w.p) || !finite3(w.n) || !finite3(w.omega) || !finite3(w.vel))
-            return fail(h, DEM_ERR_INVALID_ARG, "wall vectors must be finite");
-        const double nn = w.n[0] * w.n[0] + w.n[1] * w.n[1] + w.n[2] * w.n[2];
-        if (std::fabs(nn - 1.0) > 1e-12) return fail(h, DEM_ERR_INVALID_ARG, "wall n must be a unit vector");
-        if (w.kind == DEM_CYLINDER_IN) {
-            if (!(w.radius > 0.0)) return fail(h, DEM_ERR_INVALID_ARG, "cylinder radius must be > 0");
-            if (h->cfg.precision == DEM_FP32 && make_wall(w).axis < 0)
-                return fail(h, DEM_ERR_INVALID_ARG, "in DEM_FP32 mode a cylinder axis must be a coordinate axis");
-        }
+        std::string why;
+        if (!check_wall(walls[k], h->cfg.precision, why)) return fail(h, DEM_ERR_INVALID_ARG, why.c_str());
     }
     DeviceGuard g(h->device);
     h->walls.assign(walls, walls + nwalls);
@@ -619,6 +647,37 @@ dem_status dem_step(dem_handle* h, int64_t nsteps) {
         h->n_sort += nsteps;
     }
     return st;
+}
+
+dem_status dem_run_until(dem_handle* h, int64_t max_steps, double disp_threshold, int64_t check_every,
+                         int64_t* steps_done, double* last_max_disp, int* settled) {
+    if (!h) return DEM_ERR_INVALID_ARG;
+    if (max_steps < 0 || check_every < 1 || !(disp_threshold >= 0.0))
+        return fail(h, DEM_ERR_INVALID_ARG, "max_steps >= 0, check_every >= 1 and disp_threshold >= 0 are required");
+    int64_t done = 0;
+    double disp = 0.0;
+    int ok = 0;
+    while (done < max_steps) {
+        const int64_t k = std::min(check_every, max_steps - done);
+        const dem_status st = dem_step(h, k);
+        if (st != DEM_OK) {
+            if (steps_done) *steps_done = done + k;
+            return st;
+        }
+        done += k;
+        uint32_t bits = h->d.st_host->last.max_disp2_bits;
+        float d2;
+        std::memcpy(&d2, &bits, sizeof d2);
+        disp = std::sqrt((double)d2);
+        if (disp < disp_threshold) {
+            ok = 1;
+            break;
+        }
+    }
+    if (steps_done) *steps_done = done;
+    if (last_max_disp) *last_max_disp = disp;
+    if (settled) *settled = ok;
+    return DEM_OK;
 }
 
 dem_status dem_set_timing(dem_handle* h, int enable) {
@@ -1214,8 +1273,7 @@ dem_status dem_batch_add(dem_batch* b, const dem_config* cfg, int nwalls, const 
     if (n < 0 || n > 0x7FFFFF00 || step_budget < 0) return bfail(b, DEM_ERR_INVALID_ARG, "n or step_budget");
     if (n > 0 && (!x || !v || !w || !r)) return bfail(b, DEM_ERR_INVALID_ARG, "x, v, w and r are required");
     for (int k = 0; k < nwalls; ++k)
-        if (walls[k].kind == DEM_CYLINDER_IN && cfg->precision == DEM_FP32 && make_wall(walls[k]).axis < 0)
-            return bfail(b, DEM_ERR_INVALID_ARG, "in DEM_FP32 mode a cylinder axis must be a coordinate axis");
+        if (!check_wall(walls[k], cfg->precision, why)) return bfail(b, DEM_ERR_INVALID_ARG, why);
     BatchScene sc;
     sc.slot = b->next_slot++;
     sc.cfg = *cfg;

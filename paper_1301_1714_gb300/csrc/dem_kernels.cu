@@ -159,6 +159,22 @@ struct PF64 {
             cp = (x - a * s) - p;
             return true;
         }
+        if (W.kind == 2) {
+            // half-plate: the nearest plate point is the projection of the centre, or the
+            // edge point beside it when the projection falls off the plate
+            const V3<double> u = mk(W.u[0], W.u[1], W.u[2]);
+            const V3<double> q = x - p;
+            const double h = dot(q, a), s = dot(q, u);
+            V3<double> e = a * -h;
+            if (s < 0.0) e = e + u * -s;
+            const double dist = sqrt(dot(e, e));
+            const double d = r - dist;
+            if (!(d > 0.0)) return false;
+            n = dist > 0.0 ? e * (1.0 / dist) : a * -1.0;
+            delta = d;
+            cp = q + e;
+            return true;
+        }
         const V3<double> q = x - p;
         const double ax = dot(q, a);
         const V3<double> rho = q - a * ax;
@@ -208,7 +224,7 @@ struct PF64 {
         B.wx[q] = wn.x; B.wy[q] = wn.y; B.wz[q] = wn.z;
         B.id[q] = me.id;
         finite = isfinite(xn) && isfinite(yn) && isfinite(zn) && isfinite(vn.x) && isfinite(vn.y) && isfinite(vn.z);
-        pnew = make_float4((float)xn, (float)yn, (float)zn, 0.f);
+        pnew = make_float4((float)xn, (float)yn, (float)zn, (float)(dot(vn, vn) * (S.dt * S.dt)));
         return cell_key(S, xn, yn, zn, clamped);
     }
     static __device__ __forceinline__ V3<double> pos(const Self& m) { return mk(m.x, m.y, m.z); }
@@ -393,6 +409,61 @@ struct PF32 {
     }
     static __device__ __forceinline__ float hic(const Self& m, int a) { return a == 0 ? m.hx : (a == 1 ? m.hy : m.hz); }
     static __device__ __forceinline__ float loc(const Self& m, int a) { return a == 0 ? m.lx : (a == 1 ? m.ly : m.lz); }
+    // Half-plate whose normal (axis na) and edge-to-plate direction u (axis ua) are
+    // coordinate axes. Height h and the distance s from the edge line are float-float;
+    // over the plate (s >= 0) delta = r - |h|, beside it the nearest point is on the edge
+    // and delta = (r^2 - dist^2) / (r + dist) with dist^2 = s^2 + h^2.
+    static __device__ __noinline__ bool half_plate(const WallDev& W, const Self& me, const SceneDev& S,
+                                                      V3<float>& n, float& delta, V3<float>& cp) {
+        const float r = me.r;
+        const int na = W.axis, ua = W.uaxis, oa = 3 - W.axis - W.uaxis;
+        const float sn = W.n_hi[na], su = W.uf[ua];
+        if (fabsf(sn * (hic(me, na) - W.pf[na])) >= r + S.eps_f) return false;
+        float hh, hl, sh, sl;
+        ff_diff(hic(me, na), loc(me, na), W.p_hi[na], W.p_lo[na], hh, hl);
+        ff_diff(hic(me, ua), loc(me, ua), W.p_hi[ua], W.p_lo[ua], sh, sl);
+        hh *= sn; hl *= sn; sh *= su; sl *= su;
+        const float th = sh, tl = sl;
+        float c[3];
+        c[oa] = __fadd_rn(hic(me, oa) - W.pf[oa], loc(me, oa) - W.p_lo[oa]);
+        c[na] = 0.f;
+        float nn[3] = {0.f, 0.f, 0.f};
+        if (sh > 0.f || (sh == 0.f && sl >= 0.f)) {
+            const bool up = hh > 0.f || (hh == 0.f && hl >= 0.f);
+            float dh, de;
+            two_sum(r, up ? -hh : hh, dh, de);
+            const float d = __fadd_rn(dh, __fsub_rn(de, up ? hl : -hl));
+            if (!(d > 0.f)) return false;
+            delta = d;
+            nn[na] = up ? -sn : sn;
+            c[ua] = su * __fadd_rn(sh, sl);
+        } else {
+            float pt, pte, ph, phe, s1, e1, rr, rre, a, ae;
+            two_prod(th, th, pt, pte);
+            two_prod(hh, hh, ph, phe);
+            two_sum(pt, ph, s1, e1);
+            float rlo = __fadd_rn(e1, __fadd_rn(pte, phe));
+            rlo = __fadd_rn(rlo, __fadd_rn(__fmaf_rn(2.f * th, tl, __fmul_rn(tl, tl)),
+                                           __fmaf_rn(2.f * hh, hl, __fmul_rn(hl, hl))));
+            two_prod(r, r, rr, rre);
+            two_sum(rr, -s1, a, ae);
+            const float D = __fadd_rn(a, __fadd_rn(ae, __fsub_rn(rre, rlo)));
+            if (!(D > 0.f)) return false;
+            delta = __fdiv_rn(D, __fadd_rn(r, sqrtf(s1)));
+            const float dist = __fsub_rn(r, delta);
+            if (dist > 0.f) {
+                const float inv = __fdiv_rn(1.f, dist);
+                nn[ua] = -su * __fmul_rn(__fadd_rn(th, tl), inv);
+                nn[na] = -sn * __fmul_rn(__fadd_rn(hh, hl), inv);
+            } else {
+                nn[na] = -sn;
+            }
+            c[ua] = 0.f;
+        }
+        n = mk(nn[0], nn[1], nn[2]);
+        cp = mk(c[0], c[1], c[2]);
+        return true;
+    }
     static __device__ __forceinline__ bool wall(const WallDev& W, const Self& me, const SceneDev& S, V3<float>& n,
                                                 float& delta, V3<float>& cp) {
         const float r = me.r;
@@ -432,6 +503,7 @@ struct PF32 {
             cp = mk((u[0] + ul[0]) - s * W.nf[0], (u[1] + ul[1]) - s * W.nf[1], (u[2] + ul[2]) - s * W.nf[2]);
             return true;
         }
+        if (W.kind == 2) return half_plate(W, me, S, n, delta, cp);
         // cylinder interior with a coordinate axis
         const int ax = W.axis, b = (ax + 1) % 3, c = (ax + 2) % 3;
         const float gf = W.rad_hi - r;
@@ -523,7 +595,7 @@ struct PF32 {
         B.W[q] = make_float4(wn.x, wn.y, wn.z, 0.f);
         B.id[q] = me.id;
         finite = isfinite(hx) && isfinite(hy) && isfinite(hz) && isfinite(vn.x) && isfinite(vn.y) && isfinite(vn.z);
-        pnew = make_float4(hx, hy, hz, 0.f);
+        pnew = make_float4(hx, hy, hz, dot(vn, vn) * (S.dt_f * S.dt_f));
         return cell_key(S, hx, hy, hz, clamped);
     }
     static __device__ __forceinline__ V3<double> pos(const Self& m) {
@@ -604,7 +676,7 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
     const uint32_t q = blockIdx.x * bd + tid;
     const size_t cap = a.cap;
     uint32_t c_pp = 0, c_wc = 0, c_clamp = 0, c_nnew = 0;
-    float c_maxov = 0.f;
+    float c_maxov = 0.f, c_disp2 = 0.f;
     const bool valid = q < a.n;
     const SceneDev& S = a.scenes[valid ? scene_of(a.scenes, a.nscenes, q) : 0];
     const bool live = valid && S.active;
@@ -780,6 +852,7 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
             const uint32_t kk = PR::integrate(B, q, me, F, Tq, S, mi, clamped, finite, pnew);
             if (!finite) raise_status(a.st, ST_NONFINITE, (int32_t)q);
             c_clamp = clamped ? 1u : 0u;
+            c_disp2 = pnew.w;
             if (LIST) {
                 // a particle that moved skin/2 (less the FP32 margin) since the last sort
                 // makes this step end with a sort and new lists
@@ -799,12 +872,14 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
     const uint32_t s_cl = __reduce_add_sync(full, c_clamp);
     const uint32_t s_mx = __reduce_max_sync(full, c_nnew);
     const uint32_t s_ov = __reduce_max_sync(full, __float_as_uint(c_maxov));
+    const uint32_t s_dp = __reduce_max_sync(full, __float_as_uint(c_disp2));
     if ((tid & 31) == 0) {
         if (s_pp) atomicAdd(&a.st->live.ncontacts, s_pp);
         if (s_wc) atomicAdd(&a.st->live.nwallc, s_wc);
         if (s_cl) atomicAdd(&a.st->live.clamped, s_cl);
         if (s_mx) atomicMax(&a.st->live.max_nnew, s_mx);
         if (s_ov) atomicMax(&a.st->live.max_overlap_bits, s_ov);
+        if (s_dp) atomicMax(&a.st->live.max_disp2_bits, s_dp);
     }
 }
 

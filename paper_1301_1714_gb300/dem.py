@@ -21,7 +21,7 @@ DEM_PRACTICAL, DEM_SIMPLE = 0, 1
 DEM_LINEAR, DEM_HERTZ = 0, 1
 DEM_FP64, DEM_FP32 = 0, 1
 DEM_HOST, DEM_DEVICE = 0, 1
-DEM_PLANE, DEM_CYLINDER_IN = 0, 1
+DEM_PLANE, DEM_CYLINDER_IN, DEM_HALF_PLATE = 0, 1, 2
 DEM_TERM_NO_ATTRACTION, DEM_TERM_ROLLING, DEM_TERM_ETA_T, DEM_TERM_COHESION = 1, 2, 4, 8
 WALL_BASE = 0xFFFFFF00
 
@@ -42,7 +42,7 @@ class dem_config(ctypes.Structure):
 
 class dem_wall(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("pad", ctypes.c_int32), ("p", _D3), ("n", _D3), ("radius", ctypes.c_double),
-                ("omega", _D3), ("vel", _D3)]
+                ("omega", _D3), ("vel", _D3), ("u", _D3)]
 
 
 class DemError(RuntimeError):
@@ -52,7 +52,7 @@ class DemError(RuntimeError):
 
 
 _lib = None
-_EXPORTS = ["dem_create", "dem_set_particles", "dem_set_walls", "dem_step", "dem_get_state", "dem_get_forces",
+_EXPORTS = ["dem_create", "dem_set_particles", "dem_set_walls", "dem_step", "dem_run_until", "dem_get_state", "dem_get_forces",
             "dem_get_history", "dem_restore", "dem_get_diagnostics", "dem_debug_snapshot", "dem_get_grid",
             "dem_device_bytes", "dem_launch_count", "dem_last_error", "dem_destroy", "dem_set_timing",
             "dem_get_phase_times", "dem_sort_cells_static", "dem_batch_create", "dem_batch_add", "dem_batch_run",
@@ -78,6 +78,8 @@ def lib():
     L.dem_set_particles.argtypes = [P, I64, P, P, P, P, P, I32]
     L.dem_set_walls.argtypes = [P, I32, P]
     L.dem_step.argtypes = [P, I64]
+    L.dem_run_until.argtypes = [P, I64, ctypes.c_double, I64, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(I32)]
     L.dem_get_state.argtypes = [P, P, P, P, I32]
     L.dem_get_forces.argtypes = [P, P, P, I32]
     L.dem_get_history.argtypes = [P, I64, P, P, P, ctypes.POINTER(I64)]
@@ -113,6 +115,7 @@ def lib():
     for name in _EXPORTS:
         f = getattr(L, name)
         if f.restype is ctypes.c_int or name in ("dem_create", "dem_set_particles", "dem_set_walls", "dem_step",
+                                                  "dem_run_until",
                                                   "dem_get_state", "dem_get_forces", "dem_get_history", "dem_restore",
                                                   "dem_get_diagnostics", "dem_debug_snapshot", "dem_get_grid",
                                                   "dem_set_timing", "dem_get_phase_times",
@@ -178,12 +181,13 @@ def config_from_params(p, block_size=0, max_contacts=0) -> dem_config:
 def walls_array(walls):
     arr = (dem_wall * max(1, len(walls)))()
     for k, w in enumerate(walls):
-        arr[k].kind = {"plane": DEM_PLANE, "cylinder": DEM_CYLINDER_IN}[w["kind"]]
+        arr[k].kind = {"plane": DEM_PLANE, "cylinder": DEM_CYLINDER_IN, "half_plate": DEM_HALF_PLATE}[w["kind"]]
         for a in range(3):
             arr[k].p[a] = w["p"][a]
             arr[k].n[a] = w["n"][a]
             arr[k].omega[a] = w.get("omega", (0, 0, 0))[a]
             arr[k].vel[a] = w.get("vel", (0, 0, 0))[a]
+            arr[k].u[a] = w.get("u", (0, 0, 0))[a]
         arr[k].radius = w.get("radius", 0.0)
     return arr
 
@@ -219,6 +223,17 @@ def dem_set_walls(h, walls):
 
 def dem_step(h, nsteps=1):
     _check(h, lib().dem_step(h, int(nsteps)))
+
+
+def dem_run_until(h, max_steps, disp_threshold, check_every=100):
+    """Steps until max |v'| dt of the last step of a chunk is below disp_threshold.
+    Returns (steps_done, last_max_disp, settled)."""
+    done = ctypes.c_int64(0)
+    disp = ctypes.c_double(0.0)
+    ok = ctypes.c_int(0)
+    _check(h, lib().dem_run_until(h, int(max_steps), float(disp_threshold), int(check_every), ctypes.byref(done),
+                                  ctypes.byref(disp), ctypes.byref(ok)))
+    return int(done.value), float(disp.value), bool(ok.value)
 
 
 def dem_get_state(h, n, x=None, v=None, w=None):

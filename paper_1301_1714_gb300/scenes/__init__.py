@@ -163,9 +163,17 @@ def drum_walls(Rd, L, omega):
     ]
 
 
+def slit_plates(z, xc, half_width):
+    """A horizontal plate at height z with a slit of width 2 half_width across x, centred
+    at xc and running the whole length in y: two half-plates, touched from both sides."""
+    return [dict(kind="half_plate", p=(xc + half_width, 0.0, z), n=(0.0, 0.0, 1.0), u=(1.0, 0.0, 0.0)),
+            dict(kind="half_plate", p=(xc - half_width, 0.0, z), n=(0.0, 0.0, 1.0), u=(-1.0, 0.0, 0.0))]
+
+
 def _norm_wall(w):
     d = dict(kind=w["kind"], p=tuple(w["p"]), n=tuple(w["n"]), radius=float(w.get("radius", 0.0)),
-             omega=tuple(w.get("omega", (0.0, 0.0, 0.0))), vel=tuple(w.get("vel", (0.0, 0.0, 0.0))))
+             omega=tuple(w.get("omega", (0.0, 0.0, 0.0))), vel=tuple(w.get("vel", (0.0, 0.0, 0.0))),
+             u=tuple(w.get("u", (0.0, 0.0, 0.0))))
     return d
 
 
@@ -284,6 +292,45 @@ def box_rsa(seed: int = 1, n: int = 262_144, rbar: float = 1e-3, spread: float =
                alpha=alpha, mu=mu, ksp=kn, kda=eta, ksh=eta, cell_size=auto_cell_size(float(rad.max())),
                domain_lo=lo, domain_hi=hi, walls=[_norm_wall(q) for q in box_walls(lo, hi)])
     return Scene(f"box_rsa_{n}_s{seed}", x, v, w, rad, p)
+
+
+def hopper(seed: int = 1, nx: int = 64, ny: int = 32, nz: int = 64, r: float = 1e-3, spacing: float = 2.1,
+           jitter: float = 0.025, vsigma: float = 0.05, slit_over_d: float = 6.0, e: float = 0.5, kn: float = 1e4,
+           mu: float = 0.5, precision: str = "fp32", model: str = "practical", stiffness: str = "linear",
+           open_slit: bool = True) -> Scene:
+    """The shape of the paper's benchmark (Sec. 5): equal spheres fall from a box through
+    a slit in its bottom onto a floor (2^17 = 131,072 spheres by default; the paper gives
+    no geometry). The box has the lattice's footprint (nx x ny columns at spacing r,
+    sphere edges 0.05 r from the side walls); its bottom is a plate with a slit of width
+    2 slit_over_d r across x, centred, running the whole depth in y (two half-plates);
+    the bin below holds all spheres at solid fraction 0.43. The spheres start on the
+    jittered lattice just above the plate, velocities N(0, vsigma). With open_slit=False
+    the bottom is a closed plane instead, for filling the box at rest before the slit
+    opens. Walls: the four sides, the floor and a lid (planes), then the plate.
+    dt = contact time / 50."""
+    n = nx * ny * nz
+    W = (nx * spacing * r, ny * spacing * r)
+    bin_h = n * (4.0 / 3.0) * math.pi * r ** 3 / (0.43 * W[0] * W[1])
+    zp = math.ceil(bin_h / r) * r
+    top = zp + (1.05 + (nz - 1) * spacing + 3.0) * r
+    lo, hi = (0.0, 0.0, 0.0), (W[0], W[1], top)
+    first = np.array([0.5 * spacing * r, 0.5 * spacing * r, zp + 1.05 * r])
+    x = np.zeros((n, 3)); v = np.zeros((n, 3)); w = np.zeros((n, 3)); rad = np.zeros(n, dtype=np.float32)
+    _L().scn_lattice_box(seed, nx, ny, nz, spacing * r, jitter * r, _p(first), r, vsigma, _p(x), _p(v), _p(w), _p(rad))
+    m = sphere_mass(float(np.float32(r)))
+    dt = linear_contact_time(kn, e, 0.5 * m) / 50.0
+    alpha = alpha_from_e(e)
+    eta = alpha * math.sqrt(kn * 0.5 * m)
+    cn, ct = hertz_coeffs(kn, 2.0 / 7.0, r)
+    if open_slit:
+        plate = slit_plates(zp, 0.5 * W[0], slit_over_d * r)
+    else:
+        plate = [dict(kind="plane", p=(0.0, 0.0, zp), n=(0.0, 0.0, 1.0))]
+    walls = box_walls(lo, hi) + plate
+    p = Params(model=model, stiffness=stiffness, precision=precision, dt=dt, kn=kn, kt=kn * 2.0 / 7.0, cn=cn, ct=ct,
+               alpha=alpha, mu=mu, ksp=kn, kda=eta, ksh=eta, cell_size=auto_cell_size(float(rad.max())),
+               domain_lo=lo, domain_hi=hi, walls=[_norm_wall(q) for q in walls])
+    return Scene(f"hopper_{n}_s{seed}", x, v, w, rad, p)
 
 
 def drum(seed: int = 1, n: int = 4_194_304, rbar: float = 1e-3, spread: float = 0.1,

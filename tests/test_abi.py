@@ -73,4 +73,27 @@ def test_marshalling_of_config_and_walls():
     assert w[0].kind == dem.DEM_CYLINDER_IN and w[0].radius == sc.params.walls[0]["radius"]
     assert tuple(w[0].omega) == (2.0, 0.0, 0.0)
     assert w[1].kind == dem.DEM_PLANE and tuple(w[2].n) == (-1.0, 0.0, 0.0)
-    assert ctypes.sizeof(dem.dem_wall) == 8 + 8 * 13
+    assert w[1].u[0] == 0.0
+
+
+def test_ctypes_layouts_match_the_header(tmp_path):
+    """sizeof and field offsets of dem_config and dem_wall as gcc lays out include/dem.h
+    equal those of the ctypes mirrors in the binding."""
+    fields = {"dem_config": [f[0] for f in dem.dem_config._fields_], "dem_wall": [f[0] for f in dem.dem_wall._fields_]}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dem.h"', "int main(void) {"]
+    for t, fs in fields.items():
+        lines.append(f'printf("{t} %zu\\n", sizeof({t}));')
+        for f in fs:
+            lines.append(f'printf("{t}.{f} %zu\\n", offsetof({t}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "sizes.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "sizes"
+    import subprocess
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    out = dict(l.split() for l in subprocess.check_output([str(exe)], text=True).splitlines())
+    for t, fs in fields.items():
+        cls = getattr(dem, t)
+        assert int(out[t]) == ctypes.sizeof(cls), t
+        for f in fs:
+            assert int(out[f"{t}.{f}"]) == getattr(cls, f).offset, (t, f)

@@ -60,6 +60,11 @@ def force_scale(p, x, v, r, pairs):
         if wl["kind"] == "plane":
             s = (x - np.array(wl["p"])) @ np.array(wl["n"])
             delta = rr - s
+        elif wl["kind"] == "half_plate":
+            q = x - np.array(wl["p"])
+            h = q @ np.array(wl["n"])
+            su = q @ np.array(wl["u"])
+            delta = rr - np.hypot(h, np.minimum(su, 0.0))
         else:
             a = np.array(wl["n"])
             q = x - np.array(wl["p"])

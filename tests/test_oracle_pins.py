@@ -19,6 +19,10 @@ RHO = 2500.0
 M = RHO * 4.0 / 3.0 * math.pi * RF ** 3
 
 
+def test_oracle_records_match_their_mirrors():
+    assert oracle.struct_sizes_match()
+
+
 def params(**kw):
     base = dict(model="practical", stiffness="linear", precision="fp64", dt=1e-6, g=(0.0, 0.0, 0.0), kn=1e4,
                 kt=1e4 * 2 / 7, alpha=0.0, mu=0.3, cell_size=S.auto_cell_size(R), domain_lo=(-0.05, -0.05, -0.05),
