@@ -54,6 +54,7 @@ struct Domain {
     uint32_t* ncnt = nullptr;
     uint32_t* nl = nullptr;
     float4* ref = nullptr;         // positions at the last sort
+    uint16_t* lane = nullptr;      // force-pass thread -> particle (offset within its block), set at each sort
 
     // tangential history, double-buffered; h_cur is the buffer the next step reads
     uint32_t* hcnt[2] = {nullptr, nullptr};

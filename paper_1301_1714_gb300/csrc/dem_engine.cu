@@ -93,6 +93,7 @@ void free_particle_buffers(Domain& d) {
     d.S32[0] = d.S32[1] = StateF32{};
     d.ncnt = d.nl = nullptr;
     d.ref = nullptr;
+    d.lane = nullptr;
     for (int i = 0; i < 2; ++i) { d.hcnt[i] = nullptr; d.hpid[i] = nullptr; d.hd[i] = nullptr; }
     d.key = d.rank = d.tmp = d.perm = d.skey = d.cnt = d.cs = d.part = nullptr;
     d.diag_part = nullptr;
@@ -289,6 +290,7 @@ dem_status alloc_domain(Domain& d, uint32_t n, uint32_t ncells, std::string& err
         AL(d.ncnt, N * 4);
         AL(d.nl, N * 4 * (size_t)d.maxn);
         AL(d.ref, N * 16);
+        AL(d.lane, ((N + 1023) / 1024) * 1024 * 2);
     }
     AL(d.cnt, ((size_t)ccap + 1) * 4);
     AL(d.cs, ((size_t)ccap + 1) * 4);
@@ -965,7 +967,7 @@ int64_t dem_device_bytes(const dem_handle* h) {
     size_t b = 2 * state + 2 * (N * 4 + N * 4 * M + N * T * 3 * M) + 5 * N * 4 + 2 * C * 4 + (size_t)d.part_cap * 4 +
                (size_t)d.diag_part_cap * 80 + sizeof(StatusDev) + 128 + sizeof(SceneDev) * d.scenes_cap;
     b += (size_t)h->stage_cap * (9 * 8 + 4);
-    if (d.list_mode) b += N * (4 + 4 * (size_t)d.maxn + 16);
+    if (d.list_mode) b += N * (4 + 4 * (size_t)d.maxn + 16 + 2);
     return (int64_t)b;
 }
 

@@ -617,6 +617,7 @@ struct ForceArgs {
     const uint32_t* ncnt;        // list mode: neighbour lists of the last sort
     const uint32_t* nl;
     const float4* ref;           // list mode: positions at the last sort
+    const uint16_t* lane;        // list mode: particle (offset in the block) of each thread
     float thresh2;               // list mode: squared displacement that forces a sort
     int interval;                // list mode: sort at least every `interval` steps (0: never forced)
     const uint32_t* skey;
@@ -673,7 +674,8 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
     uint32_t* s_oid = smem;               // [maxc][bd] partner ids of the stored springs
     uint32_t* s_near = smem + maxc * bd;  // [maxc][bd] near candidates of phase 1 (walk mode)
     uint64_t near_mask = 0;               // list mode: list entries that passed phase 1
-    const uint32_t q = blockIdx.x * bd + tid;
+    // list mode: the particle of this thread comes from the block's lane order
+    const uint32_t q = blockIdx.x * bd + (LIST ? (uint32_t)__ldg(&a.lane[blockIdx.x * bd + tid]) : tid);
     const size_t cap = a.cap;
     uint32_t c_pp = 0, c_wc = 0, c_clamp = 0, c_nnew = 0;
     float c_maxov = 0.f, c_disp2 = 0.f;
@@ -1018,16 +1020,18 @@ __global__ void k_reorder(uint32_t n, typename PR::State S0, typename PR::State 
 // each particle (Eq. 12) that lies within r_i + r_j + skin (+ the FP32 margin). With
 // cells of edge >= 2 r_max + skin, no pair that comes into contact before some particle
 // has moved skin/2 is missed.
+//
+// The block (of the force pass's size) then orders its particles by their contact count
+// in the step just finished, then by list length, both descending, ties by position:
+// lane[b*bd + t] is the particle that thread t of force block b takes until the next
+// sort. The warps of the force pass run their lanes in lockstep over each lane's
+// candidates, so grouping similar counts into a warp shortens the longest lane's loop;
+// every particle's sums keep their own order, so results do not depend on this order.
 template <class PR>
-__global__ void __launch_bounds__(256) k_nlist(uint32_t n, const SceneDev* scenes, int nscenes, typename PR::State S0,
-                                                typename PR::State S1, const CtrlDev* ctrl,
-                                                const uint32_t* __restrict__ skey, const uint32_t* __restrict__ cs,
-                                                uint32_t* __restrict__ ncnt, uint32_t* __restrict__ nl, size_t cap,
-                                                uint32_t maxn, float skin, StatusDev* st) {
-    if (!ctrl->rebuild) return;
-    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
-    const typename PR::State A = ctrl->cur ? S1 : S0;
+__device__ __forceinline__ uint32_t nlist_one(uint32_t q, const SceneDev* scenes, int nscenes,
+                                              const typename PR::State& A, const uint32_t* __restrict__ skey,
+                                              const uint32_t* __restrict__ cs, uint32_t* __restrict__ nl, size_t cap,
+                                              uint32_t maxn, float skin, StatusDev* st) {
     const SceneDev& S = scenes[scene_of(scenes, nscenes, q)];
     const typename PR::Self me = PR::load(A, q);
     const float extra = skin + S.eps_f;
@@ -1056,7 +1060,35 @@ __global__ void __launch_bounds__(256) k_nlist(uint32_t n, const SceneDev* scene
             ++m;
         }
     if (m > maxn) raise_status(st, ST_CAPACITY, (int32_t)q);
-    ncnt[q] = min(m, maxn);
+    return min(m, maxn);
+}
+
+template <class PR>
+__global__ void __launch_bounds__(256) k_nlist(uint32_t n, const SceneDev* scenes, int nscenes, typename PR::State S0,
+                                                typename PR::State S1, const CtrlDev* ctrl,
+                                                const uint32_t* __restrict__ skey, const uint32_t* __restrict__ cs,
+                                                uint32_t* __restrict__ ncnt, uint32_t* __restrict__ nl, size_t cap,
+                                                uint32_t maxn, float skin, StatusDev* st,
+                                                const uint32_t* __restrict__ hcnt_last, const uint32_t* __restrict__ perm,
+                                                uint16_t* __restrict__ lane) {
+    if (!ctrl->rebuild) return;
+    __shared__ uint32_t s_key[256];
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t key = 0;
+    if (q < n) {
+        const typename PR::State A = ctrl->cur ? S1 : S0;
+        const uint32_t m = nlist_one<PR>(q, scenes, nscenes, A, skey, cs, nl, cap, maxn, skin, st);
+        ncnt[q] = m;
+        key = (min(hcnt_last[perm[q]], 255u) << 8) | min(m, 255u);
+    }
+    s_key[threadIdx.x] = key;
+    __syncthreads();
+    uint32_t rank = 0;
+    for (uint32_t t = 0; t < blockDim.x; ++t) {
+        const uint32_t kt = s_key[t];
+        rank += (kt > key || (kt == key && t < threadIdx.x)) ? 1u : 0u;
+    }
+    lane[blockIdx.x * blockDim.x + rank] = (uint16_t)threadIdx.x;
 }
 
 // Step bookkeeping (one thread): after a sort the current set stays and springs are read
@@ -1331,14 +1363,17 @@ cudaError_t run_rebuild(Domain& d) {
                                                                d.perm, d.skey, ref);
     DEM_LAUNCH_CHECK();
     if (d.list_mode) {
+        // one block per force-pass block: the lane order is per force block
+        const uint32_t b = (uint32_t)d.block;
+        const uint32_t* hc = d.hcnt[d.h_cur];   // contact counts of the step just finished (pre-sort order)
         if (d.precision == 0)
-            k_nlist<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S64[0], d.S64[1], d.ctrl,
-                                                                 d.skey, d.cs, d.ncnt, d.nl, d.cap, (uint32_t)d.maxn,
-                                                                 d.skin_f, d.st);
+            k_nlist<PF64><<<nblk(d.n, b), b, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S64[0], d.S64[1], d.ctrl,
+                                                             d.skey, d.cs, d.ncnt, d.nl, d.cap, (uint32_t)d.maxn,
+                                                             d.skin_f, d.st, hc, d.perm, d.lane);
         else
-            k_nlist<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S32[0], d.S32[1], d.ctrl,
-                                                                 d.skey, d.cs, d.ncnt, d.nl, d.cap, (uint32_t)d.maxn,
-                                                                 d.skin_f, d.st);
+            k_nlist<PF32><<<nblk(d.n, b), b, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S32[0], d.S32[1], d.ctrl,
+                                                             d.skey, d.cs, d.ncnt, d.nl, d.cap, (uint32_t)d.maxn,
+                                                             d.skin_f, d.st, hc, d.perm, d.lane);
         DEM_LAUNCH_CHECK();
     }
     return cudaSuccess;
@@ -1366,6 +1401,7 @@ static cudaError_t force_impl(Domain& d, const typename PR::State& S0, const typ
     a.ncnt = d.ncnt;
     a.nl = d.nl;
     a.ref = d.ref;
+    a.lane = d.lane;
     a.thresh2 = d.thresh2;
     a.interval = d.interval;
     a.skey = d.skey;

@@ -370,6 +370,24 @@ def test_block_size_does_not_change_results(block):
     assert np.array_equal(xa, xb) and np.array_equal(va, vb)
 
 
+@pytest.mark.parametrize("block", [32, 96, 256])
+def test_list_mode_lane_order_does_not_change_results(block):
+    """In list mode each force block takes its particles in the order the last sort chose
+    (by contact count); a particle's sums keep their own order, so any block size (and so
+    any lane order) gives the same bits, and so does the sort-every-step walk."""
+    sc = scenes.drum(seed=8, n=6000)
+    p = listed(sc.params.copy(precision="fp32"), skin_r=0.1, interval=0)
+    with sim(p, sc, block_size=256) as a:
+        a.step(200)
+        xa, va, wa = a.state()
+        sorts = a.diagnostics()["sorts"]
+    with sim(p, sc, block_size=block) as b:
+        b.step(200)
+        xb, vb, wb = b.state()
+    assert sorts > 2
+    assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(wa, wb)
+
+
 def test_capacity_overflow_is_reported():
     sc = scenes.box_lattice(seed=1)
     x = compressed(sc, 0.95)

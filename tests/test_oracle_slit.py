@@ -26,7 +26,7 @@ ZP = 0.01
 def params(half, g=(0.0, 0.0, -G), e=0.3, mu=0.3, **kw):
     tc = math.pi / math.sqrt(KN / M)
     base = dict(model="practical", stiffness="linear", precision="fp64", dt=tc / 50, g=g, kn=KN, kt=KN * 2 / 7,
-                alpha=S.alpha_from_e(e), mu=mu, cell_size=S.auto_cell_size(R), domain_lo=(-0.02, -0.02, 0.0),
+                alpha=S.alpha_from_e(e), mu=mu, cell_size=S.auto_cell_size(RF), domain_lo=(-0.02, -0.02, 0.0),
                 domain_hi=(0.02, 0.02, 0.02), walls=S.slit_plates(ZP, 0.0, half))
     base.update(kw)
     return S.Params(**base)

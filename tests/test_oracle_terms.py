@@ -26,7 +26,7 @@ G = 9.81
 
 def params(**kw):
     base = dict(model="practical", stiffness="linear", precision="fp64", dt=1e-6, g=(0.0, 0.0, 0.0), kn=KN,
-                kt=KN * 2 / 7, alpha=0.0, mu=0.3, cell_size=S.auto_cell_size(R), domain_lo=(-0.05, -0.05, -0.05),
+                kt=KN * 2 / 7, alpha=0.0, mu=0.3, cell_size=S.auto_cell_size(RF), domain_lo=(-0.05, -0.05, -0.05),
                 domain_hi=(0.05, 0.05, 0.05), walls=[])
     base.update(kw)
     return S.Params(**base)
