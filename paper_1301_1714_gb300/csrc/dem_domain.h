@@ -22,6 +22,7 @@ struct Domain {
     // configuration
     int precision = 0;   // 0 FP64, 1 FP32 (compensated positions)
     int model = 0;       // 0 practical, 1 simple
+    int sort_blocks = 0; // grid of the sort-phase kernels (a few blocks per SM)
     int terms = 0;       // union of the scenes' optional force terms (selects the kernel variant)
     int stiffness = 0;   // 0 linear, 1 Hertz
     int maxc = 32;       // history slots per particle
@@ -54,7 +55,6 @@ struct Domain {
     uint32_t* ncnt = nullptr;
     uint32_t* nl = nullptr;
     float4* ref = nullptr;         // positions at the last sort
-    uint16_t* lane = nullptr;      // force-pass thread -> particle (offset within its block), set at each sort
 
     // tangential history, double-buffered; h_cur is the buffer the next step reads
     uint32_t* hcnt[2] = {nullptr, nullptr};

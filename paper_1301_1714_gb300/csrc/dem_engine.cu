@@ -93,7 +93,6 @@ void free_particle_buffers(Domain& d) {
     d.S32[0] = d.S32[1] = StateF32{};
     d.ncnt = d.nl = nullptr;
     d.ref = nullptr;
-    d.lane = nullptr;
     for (int i = 0; i < 2; ++i) { d.hcnt[i] = nullptr; d.hpid[i] = nullptr; d.hd[i] = nullptr; }
     d.key = d.rank = d.tmp = d.perm = d.skey = d.cnt = d.cs = d.part = nullptr;
     d.diag_part = nullptr;
@@ -111,6 +110,16 @@ void split_f(double v, float& hi, float& lo) {
 }
 
 // Fill a WallDev from a dem_wall.
+// Blocks of 256 threads for the sort-phase kernels: eight per SM fill the SM.
+int sort_blocks_of(int device) {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || sms <= 0) {
+        cudaGetLastError();
+        sms = 152;
+    }
+    return 8 * sms;
+}
+
 WallDev make_wall(const dem_wall& w) {
     WallDev W{};
     W.kind = w.kind;
@@ -290,7 +299,6 @@ dem_status alloc_domain(Domain& d, uint32_t n, uint32_t ncells, std::string& err
         AL(d.ncnt, N * 4);
         AL(d.nl, N * 4 * (size_t)d.maxn);
         AL(d.ref, N * 16);
-        AL(d.lane, ((N + 1023) / 1024) * 1024 * 2);
     }
     AL(d.cnt, ((size_t)ccap + 1) * 4);
     AL(d.cs, ((size_t)ccap + 1) * 4);
@@ -548,6 +556,7 @@ dem_status dem_create(const dem_config* cfg, int device, void* cuda_stream, dem_
     d.stiffness = cfg->stiffness;
     d.maxc = cfg->max_contacts > 0 ? cfg->max_contacts : 32;
     d.block = cfg->block_size > 0 ? cfg->block_size : 256;
+    d.sort_blocks = sort_blocks_of(device);
     d.list_mode = cfg->resort_interval != 1 ? 1 : 0;
     d.interval = cfg->resort_interval;
     d.maxn = 2 * d.maxc;
@@ -967,7 +976,7 @@ int64_t dem_device_bytes(const dem_handle* h) {
     size_t b = 2 * state + 2 * (N * 4 + N * 4 * M + N * T * 3 * M) + 5 * N * 4 + 2 * C * 4 + (size_t)d.part_cap * 4 +
                (size_t)d.diag_part_cap * 80 + sizeof(StatusDev) + 128 + sizeof(SceneDev) * d.scenes_cap;
     b += (size_t)h->stage_cap * (9 * 8 + 4);
-    if (d.list_mode) b += N * (4 + 4 * (size_t)d.maxn + 16 + 2);
+    if (d.list_mode) b += N * (4 + 4 * (size_t)d.maxn + 16);
     return (int64_t)b;
 }
 
@@ -1114,6 +1123,7 @@ dem_status repack(dem_batch* b) {
     nd.maxc = od.maxc;
     nd.maxn = od.maxn;
     nd.block = od.block;
+    nd.sort_blocks = od.sort_blocks;
     nd.stream = od.stream;
     nd.list_mode = 0;
     nd.interval = 1;
@@ -1248,6 +1258,7 @@ dem_status dem_batch_create(int precision, int model, int stiffness, int max_con
     d.maxc = max_contacts > 0 ? max_contacts : 32;
     d.maxn = 2 * d.maxc;
     d.block = block_size > 0 ? block_size : 256;
+    d.sort_blocks = sort_blocks_of(device);
     d.stream = (cudaStream_t)cuda_stream;
     if (cudaMalloc(&d.st, sizeof(StatusDev)) != cudaSuccess || cudaMallocHost(&d.st_host, sizeof(StatusDev)) != cudaSuccess ||
         cudaMalloc(&d.ctrl, sizeof(CtrlDev)) != cudaSuccess || cudaMallocHost(&d.ctrl_host, sizeof(CtrlDev)) != cudaSuccess ||

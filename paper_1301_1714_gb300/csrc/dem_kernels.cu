@@ -1,12 +1,19 @@
 // Kernels of the GB300 DEM timestep and their launchers.
 //
-//   k_force      steps 5-8 + 1 + 2: 27-cell contact search (Eq. 12), contact laws
-//                (Eq. 1 or Eqs. 2-10), walls, gravity, semi-implicit Euler, new cell key
-//                CM and its rank within the cell (one thread per cell-sorted particle)
+//   k_force      steps 5-8 + 1 + 2: 27-cell contact search (Eq. 12) or neighbour list,
+//                contact laws (Eq. 1 or Eqs. 2-10), walls, gravity, semi-implicit Euler,
+//                then the new cell key CM and its rank within the cell (sort every step)
+//                or the displacement test that decides a sort (neighbour lists)
+//   k_hash       step 2 for a sort step in list mode
 //   k_scan_*     exclusive scan of per-cell counts -> dense cell-start table
 //   k_scatter    particles into cell-major slots (order within a cell still arbitrary)
 //   k_reorder    step 4: (cell, id) order (Eq. 11) and gather of every property
-//   k_import / k_export / k_hash_initial / k_diag*   set-up, read-out, diagnostics
+//   k_nlist      neighbour lists of the sorted state (list mode)
+//   k_end_step   per-step bookkeeping of the device-side step control
+//   k_import / k_export / k_diag* / k_hist_canon / k_repack   set-up, read-out,
+//                diagnostics, batch repacking
+#include <algorithm>
+
 #include <cuda_runtime.h>
 
 #include "dem_domain.h"
@@ -255,12 +262,14 @@ struct PF32 {
         m.lx = p1.x; m.ly = p1.y; m.lz = p1.z;
         m.v = mk(v.x, v.y, v.z);
         m.w = mk(w.x, w.y, w.z);
-        m.id = s.id[q];
+        m.id = __float_as_uint(p1.w);
         return m;
     }
+    // P1.w carries the bits of the particle's id (also kept in the id plane), so a partner's
+    // id arrives with its low position words.
     static __device__ __forceinline__ void store(const State& s, uint32_t q, const Self& m) {
         s.P0[q] = make_float4(m.hx, m.hy, m.hz, m.r);
-        s.P1[q] = make_float4(m.lx, m.ly, m.lz, 0.f);
+        s.P1[q] = make_float4(m.lx, m.ly, m.lz, __uint_as_float(m.id));
         s.V[q] = make_float4(m.v.x, m.v.y, m.v.z, 0.f);
         s.W[q] = make_float4(m.w.x, m.w.y, m.w.z, 0.f);
         s.id[q] = m.id;
@@ -354,7 +363,7 @@ struct PF32 {
         o.p1 = __ldg(&s.P1[j]);
         o.v = __ldg(&s.V[j]);
         o.w = __ldg(&s.W[j]);
-        o.id = __ldg(&s.id[j]);
+        o.id = __float_as_uint(o.p1.w);
         return o;
     }
     static __device__ __forceinline__ void partner_vw(const Partner& o, V3<float>& v, V3<float>& w) {
@@ -590,7 +599,7 @@ struct PF32 {
         advance(hy, ly, __fmul_rn(vn.y, S.dt_f));
         advance(hz, lz, __fmul_rn(vn.z, S.dt_f));
         B.P0[q] = make_float4(hx, hy, hz, r);
-        B.P1[q] = make_float4(lx, ly, lz, 0.f);
+        B.P1[q] = make_float4(lx, ly, lz, __uint_as_float(me.id));
         B.V[q] = make_float4(vn.x, vn.y, vn.z, 0.f);
         B.W[q] = make_float4(wn.x, wn.y, wn.z, 0.f);
         B.id[q] = me.id;
@@ -617,7 +626,6 @@ struct ForceArgs {
     const uint32_t* ncnt;        // list mode: neighbour lists of the last sort
     const uint32_t* nl;
     const float4* ref;           // list mode: positions at the last sort
-    const uint16_t* lane;        // list mode: particle (offset in the block) of each thread
     float thresh2;               // list mode: squared displacement that forces a sort
     int interval;                // list mode: sort at least every `interval` steps (0: never forced)
     const uint32_t* skey;
@@ -674,8 +682,7 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
     uint32_t* s_oid = smem;               // [maxc][bd] partner ids of the stored springs
     uint32_t* s_near = smem + maxc * bd;  // [maxc][bd] near candidates of phase 1 (walk mode)
     uint64_t near_mask = 0;               // list mode: list entries that passed phase 1
-    // list mode: the particle of this thread comes from the block's lane order
-    const uint32_t q = blockIdx.x * bd + (LIST ? (uint32_t)__ldg(&a.lane[blockIdx.x * bd + tid]) : tid);
+    const uint32_t q = blockIdx.x * bd + tid;
     const size_t cap = a.cap;
     uint32_t c_pp = 0, c_wc = 0, c_clamp = 0, c_nnew = 0;
     float c_maxov = 0.f, c_disp2 = 0.f;
@@ -893,22 +900,26 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 // Every kernel of the sort takes the step control and does nothing when this step does
 // not sort (list mode between sorts).
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __restrict__ cnt, uint32_t m,
-                                                              uint32_t* __restrict__ part, const CtrlDev* ctrl) {
+                                                              uint32_t ntiles, uint32_t* __restrict__ part,
+                                                              const CtrlDev* ctrl) {
     if (!ctrl->rebuild) return;
     __shared__ uint32_t ws[SCAN_THREADS / 32];
-    const uint32_t base = blockIdx.x * SCAN_TILE;
-    uint32_t s = 0;
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-        const uint32_t k = base + i * SCAN_THREADS + threadIdx.x;
-        if (k < m) s += cnt[k];
-    }
-    s = __reduce_add_sync(0xffffffffu, s);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int w = 0; w < SCAN_THREADS / 32; ++w) t += ws[w];
-        part[blockIdx.x] = t;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t base = tile * SCAN_TILE;
+        uint32_t s = 0;
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            const uint32_t k = base + i * SCAN_THREADS + threadIdx.x;
+            if (k < m) s += cnt[k];
+        }
+        s = __reduce_add_sync(0xffffffffu, s);
+        if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < SCAN_THREADS / 32; ++w) t += ws[w];
+            part[tile] = t;
+        }
+        __syncthreads();
     }
 }
 
@@ -939,69 +950,66 @@ __global__ void __launch_bounds__(1024) k_scan_spine(uint32_t* part, uint32_t nb
 }
 
 // cs[k] = exclusive prefix of cnt; cnt[k] = 0 for the next sort
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(uint32_t* __restrict__ cnt, uint32_t m,
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(uint32_t* __restrict__ cnt, uint32_t m, uint32_t ntiles,
                                                             const uint32_t* __restrict__ part, uint32_t* __restrict__ cs,
                                                             const CtrlDev* ctrl) {
     if (!ctrl->rebuild) return;
     __shared__ uint32_t ws[SCAN_THREADS / 32];
-    const uint32_t base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
-    uint32_t v[SCAN_ITEMS];
-    uint32_t s = 0;
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-        const uint32_t k = base + i;
-        v[i] = k < m ? cnt[k] : 0u;
-        s += v[i];
-    }
-    // block-exclusive scan of the thread sums
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint32_t inc = s;
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, off);
-        if (lane >= (uint32_t)off) inc += t;
-    }
-    if (lane == 31) ws[wid] = inc;
-    __syncthreads();
-    if (wid == 0) {
-        uint32_t w = lane < SCAN_THREADS / 32 ? ws[lane] : 0u;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t base = tile * SCAN_TILE + threadIdx.x * SCAN_ITEMS;
+        uint32_t v[SCAN_ITEMS];
+        uint32_t s = 0;
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            const uint32_t k = base + i;
+            v[i] = k < m ? cnt[k] : 0u;
+            s += v[i];
+        }
+        // block-exclusive scan of the thread sums
+        uint32_t inc = s;
         for (int off = 1; off < 32; off <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, w, off);
-            if (lane >= (uint32_t)off) w += t;
+            const uint32_t t = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= (uint32_t)off) inc += t;
         }
-        if (lane < SCAN_THREADS / 32) ws[lane] = w;
-    }
-    __syncthreads();
-    uint32_t run = part[blockIdx.x] + (inc - s) + (wid > 0 ? ws[wid - 1] : 0u);
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-        const uint32_t k = base + i;
-        if (k < m) {
-            cs[k] = run;
-            cnt[k] = 0u;
+        if (lane == 31) ws[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            uint32_t w = lane < SCAN_THREADS / 32 ? ws[lane] : 0u;
+            for (int off = 1; off < 32; off <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, w, off);
+                if (lane >= (uint32_t)off) w += t;
+            }
+            if (lane < SCAN_THREADS / 32) ws[lane] = w;
         }
-        run += v[i];
+        __syncthreads();
+        uint32_t run = part[tile] + (inc - s) + (wid > 0 ? ws[wid - 1] : 0u);
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            const uint32_t k = base + i;
+            if (k < m) {
+                cs[k] = run;
+                cnt[k] = 0u;
+            }
+            run += v[i];
+        }
+        __syncthreads();
     }
 }
 
 __global__ void k_scatter(uint32_t n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
                           const uint32_t* __restrict__ cs, uint32_t* __restrict__ tmp, const CtrlDev* ctrl) {
     if (!ctrl->rebuild) return;
-    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < n) tmp[cs[key[q]] + rank[q]] = q;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
+        tmp[cs[key[q]] + rank[q]] = q;
 }
 
 // (cell, id) order: a particle's place in its cell is the number of cell-mates with a
 // smaller id. Gathers the state from the next set (pre-sort order) into the current one,
 // records the permutation, the cell of each sorted particle and (list mode) its position.
 template <class PR>
-__global__ void k_reorder(uint32_t n, typename PR::State S0, typename PR::State S1, const CtrlDev* ctrl,
-                          const uint32_t* __restrict__ key, const uint32_t* __restrict__ cs,
-                          const uint32_t* __restrict__ tmp, uint32_t* __restrict__ perm, uint32_t* __restrict__ skey,
-                          float4* __restrict__ ref) {
-    if (!ctrl->rebuild) return;
-    const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
-    const int cur = ctrl->cur;
-    const typename PR::State A = cur ? S1 : S0;
-    const typename PR::State B = cur ? S0 : S1;
+__device__ __forceinline__ void reorder_one(uint32_t s, const typename PR::State& A, const typename PR::State& B,
+                                            const uint32_t* __restrict__ key, const uint32_t* __restrict__ cs,
+                                            const uint32_t* __restrict__ tmp, uint32_t* __restrict__ perm,
+                                            uint32_t* __restrict__ skey, float4* __restrict__ ref) {
     const uint32_t p = tmp[s];
     const uint32_t c = key[p];
     const uint32_t lo = cs[c], hi = cs[c + 1];
@@ -1016,17 +1024,23 @@ __global__ void k_reorder(uint32_t n, typename PR::State S0, typename PR::State 
     if (ref) ref[q] = PR::pos_f(m);
 }
 
+template <class PR>
+__global__ void k_reorder(uint32_t n, typename PR::State S0, typename PR::State S1, const CtrlDev* ctrl,
+                          const uint32_t* __restrict__ key, const uint32_t* __restrict__ cs,
+                          const uint32_t* __restrict__ tmp, uint32_t* __restrict__ perm, uint32_t* __restrict__ skey,
+                          float4* __restrict__ ref) {
+    if (!ctrl->rebuild) return;
+    const int cur = ctrl->cur;
+    const typename PR::State A = cur ? S1 : S0;
+    const typename PR::State B = cur ? S0 : S1;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x)
+        reorder_one<PR>(s, A, B, key, cs, tmp, perm, skey, ref);
+}
+
 // Neighbour lists of the sorted state (list mode): every particle of the 27 cells around
 // each particle (Eq. 12) that lies within r_i + r_j + skin (+ the FP32 margin). With
 // cells of edge >= 2 r_max + skin, no pair that comes into contact before some particle
 // has moved skin/2 is missed.
-//
-// The block (of the force pass's size) then orders its particles by their contact count
-// in the step just finished, then by list length, both descending, ties by position:
-// lane[b*bd + t] is the particle that thread t of force block b takes until the next
-// sort. The warps of the force pass run their lanes in lockstep over each lane's
-// candidates, so grouping similar counts into a warp shortens the longest lane's loop;
-// every particle's sums keep their own order, so results do not depend on this order.
 template <class PR>
 __device__ __forceinline__ uint32_t nlist_one(uint32_t q, const SceneDev* scenes, int nscenes,
                                               const typename PR::State& A, const uint32_t* __restrict__ skey,
@@ -1068,27 +1082,11 @@ __global__ void __launch_bounds__(256) k_nlist(uint32_t n, const SceneDev* scene
                                                 typename PR::State S1, const CtrlDev* ctrl,
                                                 const uint32_t* __restrict__ skey, const uint32_t* __restrict__ cs,
                                                 uint32_t* __restrict__ ncnt, uint32_t* __restrict__ nl, size_t cap,
-                                                uint32_t maxn, float skin, StatusDev* st,
-                                                const uint32_t* __restrict__ hcnt_last, const uint32_t* __restrict__ perm,
-                                                uint16_t* __restrict__ lane) {
+                                                uint32_t maxn, float skin, StatusDev* st) {
     if (!ctrl->rebuild) return;
-    __shared__ uint32_t s_key[256];
-    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t key = 0;
-    if (q < n) {
-        const typename PR::State A = ctrl->cur ? S1 : S0;
-        const uint32_t m = nlist_one<PR>(q, scenes, nscenes, A, skey, cs, nl, cap, maxn, skin, st);
-        ncnt[q] = m;
-        key = (min(hcnt_last[perm[q]], 255u) << 8) | min(m, 255u);
-    }
-    s_key[threadIdx.x] = key;
-    __syncthreads();
-    uint32_t rank = 0;
-    for (uint32_t t = 0; t < blockDim.x; ++t) {
-        const uint32_t kt = s_key[t];
-        rank += (kt > key || (kt == key && t < threadIdx.x)) ? 1u : 0u;
-    }
-    lane[blockIdx.x * blockDim.x + rank] = (uint16_t)threadIdx.x;
+    const typename PR::State A = ctrl->cur ? S1 : S0;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
+        ncnt[q] = nlist_one<PR>(q, scenes, nscenes, A, skey, cs, nl, cap, maxn, skin, st);
 }
 
 // Step bookkeeping (one thread): after a sort the current set stays and springs are read
@@ -1139,7 +1137,7 @@ __global__ void k_import<PF32>(uint32_t n, StateF32 B, const double* __restrict_
     float h[3], l[3];
     for (int a = 0; a < 3; ++a) split_ff(x[3 * (size_t)k + a], h[a], l[a]);
     B.P0[k] = make_float4(h[0], h[1], h[2], r[k]);
-    B.P1[k] = make_float4(l[0], l[1], l[2], 0.f);
+    B.P1[k] = make_float4(l[0], l[1], l[2], __uint_as_float(k));
     B.V[k] = make_float4((float)v[3 * (size_t)k], (float)v[3 * (size_t)k + 1], (float)v[3 * (size_t)k + 2], 0.f);
     B.W[k] = make_float4((float)w[3 * (size_t)k], (float)w[3 * (size_t)k + 1], (float)w[3 * (size_t)k + 2], 0.f);
     B.id[k] = k;
@@ -1151,15 +1149,15 @@ __global__ void k_hash(uint32_t n, const SceneDev* scenes, int nscenes, typename
                        const CtrlDev* ctrl, uint32_t* __restrict__ key, uint32_t* __restrict__ rank,
                        uint32_t* __restrict__ cnt, StatusDev* st) {
     if (!ctrl->rebuild) return;
-    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n) return;
     const typename PR::State B = ctrl->cur ? S0 : S1;
-    const SceneDev& S = scenes[scene_of(scenes, nscenes, q)];
-    bool clamped = false;
-    const uint32_t kk = PR::key_of(B, S, q, clamped);
-    if (clamped) atomicAdd(&st->live.clamped, 1u);
-    key[q] = kk;
-    rank[q] = atomicAdd(&cnt[kk], 1u);
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const SceneDev& S = scenes[scene_of(scenes, nscenes, q)];
+        bool clamped = false;
+        const uint32_t kk = PR::key_of(B, S, q, clamped);
+        if (clamped) atomicAdd(&st->live.clamped, 1u);
+        key[q] = kk;
+        rank[q] = atomicAdd(&cnt[kk], 1u);
+    }
 }
 
 template <class PR>
@@ -1313,6 +1311,11 @@ static inline StateF32 shifted(StateF32 s, uint32_t p0) {
 
 // ======================================================================= launchers
 static inline uint32_t nblk(uint32_t n, uint32_t b) { return (n + b - 1) / b; }
+// Grid of the sort-phase kernels: they loop over their items, so a grid of a few blocks
+// per SM does the work of a sort, and a step that does not sort pays for few blocks.
+static inline uint32_t sgrid(const Domain& d, uint32_t n) {
+    return std::max(1u, std::min(nblk(n, 256), (uint32_t)std::max(d.sort_blocks, 1)));
+}
 
 #define DEM_LAUNCH_CHECK()                          \
     do {                                            \
@@ -1333,10 +1336,10 @@ cudaError_t run_import(Domain& d, const double* x, const double* v, const double
 cudaError_t run_hash(Domain& d) {
     if (d.n == 0) return cudaSuccess;
     if (d.precision == 0)
-        k_hash<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S64[0], d.S64[1], d.ctrl,
+        k_hash<PF64><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S64[0], d.S64[1], d.ctrl,
                                                             d.key, d.rank, d.cnt, d.st);
     else
-        k_hash<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S32[0], d.S32[1], d.ctrl,
+        k_hash<PF32><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S32[0], d.S32[1], d.ctrl,
                                                             d.key, d.rank, d.cnt, d.st);
     DEM_LAUNCH_CHECK();
     return cudaSuccess;
@@ -1346,34 +1349,32 @@ cudaError_t run_rebuild(Domain& d) {
     if (d.n == 0) return cudaSuccess;
     const uint32_t m = d.ncells + 1;
     const uint32_t nb = nblk(m, SCAN_TILE);
-    k_scan_reduce<<<nb, SCAN_THREADS, 0, d.stream>>>(d.cnt, m, d.part, d.ctrl);
+    const uint32_t gb = std::min(nb, (uint32_t)std::max(d.sort_blocks, 1));
+    k_scan_reduce<<<gb, SCAN_THREADS, 0, d.stream>>>(d.cnt, m, nb, d.part, d.ctrl);
     DEM_LAUNCH_CHECK();
     k_scan_spine<<<1, 1024, 0, d.stream>>>(d.part, nb, d.ctrl);
     DEM_LAUNCH_CHECK();
-    k_scan_down<<<nb, SCAN_THREADS, 0, d.stream>>>(d.cnt, m, d.part, d.cs, d.ctrl);
+    k_scan_down<<<gb, SCAN_THREADS, 0, d.stream>>>(d.cnt, m, nb, d.part, d.cs, d.ctrl);
     DEM_LAUNCH_CHECK();
-    k_scatter<<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.key, d.rank, d.cs, d.tmp, d.ctrl);
+    k_scatter<<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.key, d.rank, d.cs, d.tmp, d.ctrl);
     DEM_LAUNCH_CHECK();
     float4* ref = d.list_mode ? d.ref : nullptr;
     if (d.precision == 0)
-        k_reorder<PF64><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.S64[0], d.S64[1], d.ctrl, d.key, d.cs, d.tmp,
+        k_reorder<PF64><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.S64[0], d.S64[1], d.ctrl, d.key, d.cs, d.tmp,
                                                                d.perm, d.skey, ref);
     else
-        k_reorder<PF32><<<nblk(d.n, 256), 256, 0, d.stream>>>(d.n, d.S32[0], d.S32[1], d.ctrl, d.key, d.cs, d.tmp,
+        k_reorder<PF32><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.S32[0], d.S32[1], d.ctrl, d.key, d.cs, d.tmp,
                                                                d.perm, d.skey, ref);
     DEM_LAUNCH_CHECK();
     if (d.list_mode) {
-        // one block per force-pass block: the lane order is per force block
-        const uint32_t b = (uint32_t)d.block;
-        const uint32_t* hc = d.hcnt[d.h_cur];   // contact counts of the step just finished (pre-sort order)
         if (d.precision == 0)
-            k_nlist<PF64><<<nblk(d.n, b), b, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S64[0], d.S64[1], d.ctrl,
-                                                             d.skey, d.cs, d.ncnt, d.nl, d.cap, (uint32_t)d.maxn,
-                                                             d.skin_f, d.st, hc, d.perm, d.lane);
+            k_nlist<PF64><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S64[0], d.S64[1], d.ctrl,
+                                                                 d.skey, d.cs, d.ncnt, d.nl, d.cap, (uint32_t)d.maxn,
+                                                                 d.skin_f, d.st);
         else
-            k_nlist<PF32><<<nblk(d.n, b), b, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S32[0], d.S32[1], d.ctrl,
-                                                             d.skey, d.cs, d.ncnt, d.nl, d.cap, (uint32_t)d.maxn,
-                                                             d.skin_f, d.st, hc, d.perm, d.lane);
+            k_nlist<PF32><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S32[0], d.S32[1], d.ctrl,
+                                                                 d.skey, d.cs, d.ncnt, d.nl, d.cap, (uint32_t)d.maxn,
+                                                                 d.skin_f, d.st);
         DEM_LAUNCH_CHECK();
     }
     return cudaSuccess;
@@ -1401,7 +1402,6 @@ static cudaError_t force_impl(Domain& d, const typename PR::State& S0, const typ
     a.ncnt = d.ncnt;
     a.nl = d.nl;
     a.ref = d.ref;
-    a.lane = d.lane;
     a.thresh2 = d.thresh2;
     a.interval = d.interval;
     a.skey = d.skey;

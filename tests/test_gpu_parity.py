@@ -371,10 +371,9 @@ def test_block_size_does_not_change_results(block):
 
 
 @pytest.mark.parametrize("block", [32, 96, 256])
-def test_list_mode_lane_order_does_not_change_results(block):
-    """In list mode each force block takes its particles in the order the last sort chose
-    (by contact count); a particle's sums keep their own order, so any block size (and so
-    any lane order) gives the same bits, and so does the sort-every-step walk."""
+def test_list_mode_block_size_does_not_change_results(block):
+    """In list mode a particle's sums run over its own list in list order, so any block
+    size gives the same bits."""
     sc = scenes.drum(seed=8, n=6000)
     p = listed(sc.params.copy(precision="fp32"), skin_r=0.1, interval=0)
     with sim(p, sc, block_size=256) as a:

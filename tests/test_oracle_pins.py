@@ -6,6 +6,7 @@ Hertz peak overlaps, rolling/sliding kinematics, energy and momentum balances, c
 geometry and brute force against the grid.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -422,6 +423,17 @@ def fcc(nc, a):
     return np.array(pts)
 
 
+def paper_values():
+    out = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_values.txt")
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            k, v = (t.strip() for t in line.split("="))
+            out[k] = float(v)
+    return out
+
+
 def test_fcc_close_packing_counts():
     """Sec. 6, Eq. 13: an FCC packing of diameter-d spheres has sqrt(2) spheres per d^3 cell,
     a sphere touches at most 12 others, and a 27-cell neighbourhood holds on average
@@ -437,13 +449,14 @@ def test_fcc_close_packing_counts():
     p = params(cell_size=d, domain_lo=(0.0, 0.0, 0.0), domain_hi=(L, L, L))
     pairs, cand = oracle.pairs_grid(p, x, r, with_candidates=True)
     deg = np.bincount(pairs.ravel(), minlength=len(x))
-    assert deg.max() == 12
+    gold = paper_values()
+    assert deg.max() == gold["max_simultaneous_contacts"]
     interior = np.all((x > 1.5 * a) & (x < (nc - 1.5) * a), axis=1)
-    assert np.all(deg[interior] == 12)
-    # density: spheres per d^3 in the interior block
-    assert len(x) / (nc * a) ** 3 * d ** 3 == pytest.approx(math.sqrt(2.0), rel=1e-9)
+    assert np.all(deg[interior] == gold["max_simultaneous_contacts"])
+    # density: spheres per d^3 cell in the interior block (Eq. 13 with L = d)
+    assert len(x) / (nc * a) ** 3 * d ** 3 == pytest.approx(gold["spheres_per_cell_at_edge_d"], rel=1e-9)
     cin = cand[interior] + 1
-    assert np.mean(cin) == pytest.approx(27 * math.sqrt(2.0), rel=0.05)
+    assert np.mean(cin) == pytest.approx(gold["cells_walked"] * gold["spheres_per_cell_at_edge_d"], rel=0.05)
     assert cin.min() >= 13
 
 

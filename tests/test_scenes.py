@@ -67,3 +67,34 @@ def test_drum_dense_bed():
     area = Rd * Rd * math.acos(-h / Rd) + h * math.sqrt(Rd * Rd - h * h)
     phi = np.sum(4 / 3 * math.pi * r[sel] ** 3) / (area * L)
     assert 0.5 < phi < 0.7
+
+
+def test_hopper_scene():
+    """The hopper: 2^17 equal spheres (the paper's count, Sec. 5) above a plate with a
+    slit; no overlaps, every sphere inside the box and above the plate; the bin below
+    the plate holds them all at solid fraction 0.43; the two half-plates face each other
+    across a slit of 2 slit_over_d r."""
+    import os
+    sc = S.hopper()
+    gold = {}
+    for line in open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "paper_values.txt")):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            k, v = (t.strip() for t in line.split("="))
+            gold[k] = float(v)
+    assert sc.n == gold["benchmark_particles"]
+    assert S.count_overlaps(sc.x, sc.r) == 0
+    walls = sc.params.walls
+    assert len(walls) == 8 and walls[6]["kind"] == walls[7]["kind"] == "half_plate"
+    zp = walls[6]["p"][2]
+    r = sc.r.astype(np.float64)[:, None]
+    hi = np.array(sc.params.domain_hi)
+    assert np.all(sc.x - r > 0) and np.all(sc.x + r < hi)
+    assert np.all(sc.x[:, 2] - sc.r > zp)
+    W = hi[0] * hi[1]
+    assert sc.n * 4 / 3 * math.pi * 1e-9 / (W * zp) <= 0.43 + 1e-9
+    assert walls[6]["p"][0] - walls[7]["p"][0] == __import__("pytest").approx(12e-3)
+    assert walls[6]["u"] == (1.0, 0.0, 0.0) and walls[7]["u"] == (-1.0, 0.0, 0.0)
+    closed = S.hopper(open_slit=False)
+    assert len(closed.params.walls) == 7 and closed.params.walls[6]["kind"] == "plane"
+    assert np.array_equal(closed.x, sc.x)
