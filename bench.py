@@ -57,6 +57,8 @@ def parse():
                          "neighbour lists); 1 = every step (Sec. 4.2); 0 = when a particle moved skin/2; K > 1 = "
                          "at least every K steps")
     ap.add_argument("--skin-r", type=float, default=0.1, help="skin in largest radii (used when --resort is 0 or K)")
+    ap.add_argument("--max-contacts", type=int, default=0, help="per-particle contact capacity (0 = library default)")
+    ap.add_argument("--block", type=int, default=0, help="force-kernel block size when not autotuned (0 = default)")
     ap.add_argument("--simple-steps", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -402,10 +404,10 @@ def run_ours(args):
                  "table": [[c.block, c.resort, c.skin_frac, round(c.ms_per_step, 4)] for c in table]}
     else:
         k = int(args.resort)
-        block = 0
+        block = args.block
         p = sc.params if k == 1 else sc.params.copy(resort_interval=k, skin=args.skin_r * rmax,
                                                     cell_size=sc.params.cell_size + args.skin_r * rmax)
-    cfg = dem.config_from_params(p, block_size=block)
+    cfg = dem.config_from_params(p, block_size=block, max_contacts=args.max_contacts)
     h = dem.dem_create(cfg, dev.index, stream.cuda_stream)
     try:
         dem.dem_set_walls(h, p.walls)

@@ -104,10 +104,13 @@ def test_run_until_stops_at_the_oracle_step(precision):
     assert g_ok and g_disp < thr
     if precision == "fp64":
         assert g_done == done
+        assert np.max(np.abs(xs - ref.x)) <= 1e-12
     else:
-        # FP32 velocities reach the threshold within a chunk or two of the FP64 run
-        assert abs(g_done - done) <= 2 * 250
-    assert np.max(np.abs(xs - ref.x)) <= (1e-12 if precision == "fp64" else 1e-9)
+        # FP32 velocities cross the threshold within a few chunks of the FP64 run (the
+        # last small bounces differ), and the sphere is then within 1e-3 r of rest
+        assert abs(g_done - done) <= 4 * 250
+        rest = ZP + float(r[0]) - 2500.0 * 4.0 / 3.0 * np.pi * float(r[0]) ** 3 * 9.81 / 1e4
+        assert abs(xs[0, 2] - rest) <= 1e-6
 
 
 def test_run_until_respects_max_steps_and_validates():
