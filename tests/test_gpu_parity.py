@@ -375,12 +375,13 @@ def test_list_mode_block_size_does_not_change_results(block):
     """In list mode a particle's sums run over its own list in list order, so any block
     size gives the same bits."""
     sc = scenes.drum(seed=8, n=6000)
+    v = np.random.default_rng(8).normal(0.0, 1.0, size=sc.x.shape)     # stirred: several sorts
     p = listed(sc.params.copy(precision="fp32"), skin_r=0.1, interval=0)
-    with sim(p, sc, block_size=256) as a:
+    with dem.Simulation(p, sc.x, v, sc.w, sc.r, block_size=256) as a:
         a.step(200)
         xa, va, wa = a.state()
         sorts = a.diagnostics()["sorts"]
-    with sim(p, sc, block_size=block) as b:
+    with dem.Simulation(p, sc.x, v, sc.w, sc.r, block_size=block) as b:
         b.step(200)
         xb, vb, wb = b.state()
     assert sorts > 2
