@@ -298,7 +298,9 @@ dem_status dem_sort_cells_static(int64_t n, const double* x, const double* origi
 /* Bytes of device memory held by the handle. */
 int64_t dem_device_bytes(const dem_handle* h);
 
-/* Number of kernel launches the handle has enqueued so far. */
+/* Number of kernel launches the handle has enqueued so far (kernels that a replayed step
+ * graph ran conditionally are counted from a device-side counter: the call synchronises
+ * the handle's stream). */
 int64_t dem_launch_count(const dem_handle* h);
 
 /* Last error message of the handle ("" if none). Valid until the next call on h. */

@@ -80,7 +80,8 @@ struct CtrlDev {
     int32_t perm_valid;  // 1: the last step sorted, so stored springs are read through perm
     int32_t since;       // steps since the last sort
     uint32_t nsorts;     // sorts performed since the particles were set
-    int32_t pad[3];
+    uint32_t cond_sorts; // sorts run as the conditional body of a step graph (launch accounting)
+    int32_t pad[2];
 };
 
 __device__ __forceinline__ void raise_status(StatusDev* st, int32_t code, int32_t where) {

@@ -84,11 +84,16 @@ struct Domain {
 // A CUDA graph of two captured timesteps and the kernel launches it holds.
 struct StepGraph {
     cudaGraphExec_t exec = nullptr;
-    int64_t launches = 0;
+    int64_t launches = 0;        // kernels every replay launches
+    int64_t body_launches = 0;   // kernels of one conditional sort body (list mode)
+    cudaStream_t side = nullptr; // stream on which the conditional bodies are captured
     void reset() {
         if (exec) cudaGraphExecDestroy(exec);
         exec = nullptr;
         launches = 0;
+        body_launches = 0;
+        if (side) cudaStreamDestroy(side);
+        side = nullptr;
     }
 };
 
@@ -97,6 +102,7 @@ cudaError_t run_import(Domain& d, const double* x, const double* v, const double
 cudaError_t run_hash(Domain& d);      // cell key + in-cell rank of the next state (if sorting)
 cudaError_t run_rebuild(Domain& d);   // scan, scatter, (cell, id) gather, lists (if sorting)
 cudaError_t run_end_step(Domain& d);  // step bookkeeping (swap or keep, counters)
+cudaError_t run_sort_cond(Domain& d, cudaGraphConditionalHandle h);  // graph condition = this step sorts
 cudaError_t run_force(Domain& d, bool eval, double* dbgF, double* dbgT);
 cudaError_t run_export(Domain& d, double* x, double* v, double* w);
 cudaError_t run_diag(Domain& d);   // fills d.diag_out[0..9] (device)

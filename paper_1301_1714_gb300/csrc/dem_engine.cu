@@ -488,8 +488,85 @@ cudaError_t enqueue_step(Domain& d) {
     return run_end_step(d);
 }
 
+// One step for a graph in list mode: force pass, the kernel that sets the condition, a
+// conditional node whose body (captured on the side stream) is the sort and the new
+// lists, then the bookkeeping. A step that does not sort launches three kernels.
+cudaError_t capture_step_cond(Domain& d, StepGraph* g, int64_t& body) {
+    cudaError_t e;
+    if ((e = run_force(d, false, nullptr, nullptr)) != cudaSuccess) return e;
+    d.h_cur = 1 - d.h_cur;
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t graph = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    if ((e = cudaStreamGetCaptureInfo(d.stream, &cs, nullptr, &graph, &deps, nullptr, &ndeps)) != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphConditionalHandle hc;
+    if ((e = cudaGraphConditionalHandleCreate(&hc, graph, 0, 0)) != cudaSuccess) return e;
+    if ((e = run_sort_cond(d, hc)) != cudaSuccess) return e;
+    if ((e = cudaStreamGetCaptureInfo(d.stream, &cs, nullptr, &graph, &deps, nullptr, &ndeps)) != cudaSuccess) return e;
+    cudaGraphNodeParams p{};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = hc;
+    p.conditional.type = cudaGraphCondTypeIf;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &p)) != cudaSuccess) return e;
+    if ((e = cudaStreamUpdateCaptureDependencies(d.stream, &node, nullptr, 1, cudaStreamSetCaptureDependencies)) !=
+        cudaSuccess)
+        return e;
+    cudaGraph_t bg = p.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(g->side, bg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal)) !=
+        cudaSuccess)
+        return e;
+    const cudaStream_t main = d.stream;
+    const int64_t l0 = d.launches;
+    d.stream = g->side;
+    cudaError_t e1 = run_hash(d);
+    if (e1 == cudaSuccess) e1 = run_rebuild(d);
+    d.stream = main;
+    body = d.launches - l0;
+    d.launches = l0;
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(g->side, &out);
+    if (e1 != cudaSuccess) return e1;
+    if (e != cudaSuccess) return e;
+    return run_end_step(d);
+}
+
 // Two timesteps captured once as a CUDA graph (two, so that the history buffers return
 // to their starting roles) and replayed; plain launches on the legacy default stream.
+// In list mode the sort of each step is a conditional node (see capture_step_cond); if
+// the driver refuses conditional nodes the plain two-step graph is used.
+cudaError_t capture_cond_graph(Domain& d, StepGraph* g) {
+    cudaError_t e;
+    if (!g->side && (e = cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking)) != cudaSuccess) {
+        g->side = nullptr;
+        return e;
+    }
+    const int64_t l0 = d.launches;
+    const int hc0 = d.h_cur;
+    if ((e = cudaStreamBeginCapture(d.stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    int64_t b1 = 0, b2 = 0;
+    cudaError_t e1 = capture_step_cond(d, g, b1);
+    cudaError_t e2 = e1 == cudaSuccess ? capture_step_cond(d, g, b2) : e1;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(d.stream, &graph);
+    if (e1 == cudaSuccess && e2 == cudaSuccess && e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    const cudaError_t bad = e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e);
+    if (bad != cudaSuccess) {
+        g->exec = nullptr;
+        d.launches = l0;
+        d.h_cur = hc0;
+        return bad;
+    }
+    g->launches = d.launches - l0;
+    g->body_launches = b1;
+    d.launches = l0;
+    return cudaSuccess;
+}
+
 cudaError_t run_steps(Domain& d, StepGraph* g, int64_t nsteps) {
     cudaError_t e;
     if (!g || !d.stream || d.n == 0) {
@@ -500,6 +577,12 @@ cudaError_t run_steps(Domain& d, StepGraph* g, int64_t nsteps) {
     if (d.h_cur == 1 && nsteps > 0) {
         if ((e = enqueue_step(d)) != cudaSuccess) return e;
         --nsteps;
+    }
+    if (nsteps >= 2 && !g->exec && d.list_mode) {
+        if (capture_cond_graph(d, g) != cudaSuccess) {
+            cudaGetLastError();   // conditional nodes unavailable: fall back to the plain graph
+            g->reset();
+        }
     }
     if (nsteps >= 2 && !g->exec) {
         const int64_t l0 = d.launches;
@@ -980,7 +1063,21 @@ int64_t dem_device_bytes(const dem_handle* h) {
     return (int64_t)b;
 }
 
-int64_t dem_launch_count(const dem_handle* h) { return h ? h->d.launches : 0; }
+int64_t dem_launch_count(const dem_handle* h) {
+    if (!h) return 0;
+    int64_t n = h->d.launches;
+    if (h->graph.body_launches > 0 && h->d.ctrl) {
+        // sorts that ran as conditional graph bodies (counted on the device)
+        CtrlDev c{};
+        DeviceGuard g(h->device);
+        if (cudaMemcpyAsync(&c, h->d.ctrl, sizeof c, cudaMemcpyDeviceToHost, h->d.stream) == cudaSuccess &&
+            cudaStreamSynchronize(h->d.stream) == cudaSuccess)
+            n += h->graph.body_launches * (int64_t)c.cond_sorts;
+        else
+            cudaGetLastError();
+    }
+    return n;
+}
 
 const char* dem_last_error(const dem_handle* h) { return h ? h->err.c_str() : "null handle"; }
 

@@ -1380,6 +1380,20 @@ cudaError_t run_rebuild(Domain& d) {
     return cudaSuccess;
 }
 
+// Sets the condition of the step graph's sort node from the device-side decision, and
+// counts the sorts that run that way (one thread).
+__global__ void k_sort_cond(cudaGraphConditionalHandle h, CtrlDev* ctrl) {
+    const unsigned int go = ctrl->rebuild ? 1u : 0u;
+    ctrl->cond_sorts += go;
+    cudaGraphSetConditional(h, go);
+}
+
+cudaError_t run_sort_cond(Domain& d, cudaGraphConditionalHandle h) {
+    k_sort_cond<<<1, 1, 0, d.stream>>>(h, d.ctrl);
+    DEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
 cudaError_t run_end_step(Domain& d) {
     k_end_step<<<1, 1, 0, d.stream>>>(d.ctrl, d.st, d.list_mode ? 0 : 1);
     DEM_LAUNCH_CHECK();

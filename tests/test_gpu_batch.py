@@ -94,6 +94,34 @@ def test_graph_replay_equals_plain_launches(torch_cuda):
     assert np.array_equal(xa, xb)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_list_mode_graph_with_conditional_sort_equals_plain_launches(torch_cuda, precision):
+    """In list mode the replayed step graph runs the sort as a conditional node whose
+    condition the device sets; the result equals plain launches bit for bit, and the
+    launch count includes exactly the sorts that ran."""
+    torch = torch_cuda
+    stream = torch.cuda.Stream()
+    sc = scenes.drum(seed=9, n=5000, precision=precision)
+    v = np.random.default_rng(9).normal(0.0, 1.0, size=sc.x.shape)
+    skin = 0.1e-3
+    p = sc.params.copy(resort_interval=0, skin=skin, cell_size=sc.params.cell_size + skin)
+    out = []
+    for st in (None, stream.cuda_stream):
+        with dem.Simulation(p, sc.x, v, sc.w, sc.r, cuda_stream=st) as s:
+            l0 = dem.dem_launch_count(s.h)
+            s0 = s.diagnostics()["sorts"]
+            s.step(241)
+            out.append((s.state(), dem.dem_launch_count(s.h) - l0, s.diagnostics()["sorts"] - s0))
+    (a, la, sa), (b, lb, sb) = out
+    for u, w in zip(a, b):
+        assert np.array_equal(u, w)
+    assert sa == sb and sa >= 3
+    # plain: 9 kernels per step; graph: force, condition, bookkeeping per step, plus the
+    # 6 sort kernels of each sort (the first and odd last steps run plain)
+    assert la == 241 * 9
+    assert lb < la and lb >= 241 * 3
+
+
 def test_cancelled_scene_leaves_others_unchanged(torch_cuda):
     """A request cancelled mid-run (removed before its budget) does not disturb the rest."""
     torch = torch_cuda
