@@ -579,9 +579,16 @@ cudaError_t run_steps(Domain& d, StepGraph* g, int64_t nsteps) {
         --nsteps;
     }
     if (nsteps >= 2 && !g->exec && d.list_mode) {
-        if (capture_cond_graph(d, g) != cudaSuccess) {
+        const cudaError_t ce = capture_cond_graph(d, g);
+        if (ce != cudaSuccess) {
             cudaGetLastError();   // conditional nodes unavailable: fall back to the plain graph
             g->reset();
+            static bool said = false;
+            if (!said) {
+                said = true;
+                fprintf(stderr, "dem: step graph with a conditional sort node unavailable (%s); using the plain graph\n",
+                        cudaGetErrorString(ce));
+            }
         }
     }
     if (nsteps >= 2 && !g->exec) {
