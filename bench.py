@@ -438,6 +438,20 @@ def run_ours(args):
         phase = dem.dem_get_phase_times(h)
         dem.dem_set_timing(h, False)
         diag = dict(zip(dem.DIAG_NAMES, dem.dem_get_diagnostics(h)))
+        # the same number of steps again, replayed as the library's step graph (no events
+        # between phases; in list mode the sort is a conditional node)
+        torch.cuda.synchronize(dev)
+        lg0 = dem.dem_launch_count(h)
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        dem.dem_step(h, args.steps)
+        g1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_graph = replicas.reduce_max(g0.elapsed_time(g1), dev)
+        graph = {"value": round(replicas.reduce_sum(float(N), dev) * args.steps / (ms_graph / 1e3), 1),
+                 "ms_per_step": round(ms_graph / args.steps, 4),
+                 "gpu_launches": int(dem.dem_launch_count(h) - lg0)}
         ms = replicas.reduce_max(ms, dev)            # the slowest replica sets the time
         n_total = replicas.reduce_sum(float(N), dev)  # particles advanced by all replicas
         value = n_total * args.steps / (ms / 1e3)
@@ -549,7 +563,8 @@ def run_ours(args):
                           "sorts_in_timed_steps": int(sorts_timed),
                           "l2": "inputs larger than L2 (no flush needed)",
                           "device_bytes": dem.dem_device_bytes(h), "parallelism": f"replicas x{world}"},
-               "roofline": roof, "gpu_launches": int(launches), "clocks": clocks, "simple": simple, "e2e": e2e,
+               "roofline": roof, "gpu_launches": int(launches), "clocks": clocks, "graph_replay": graph,
+               "simple": simple, "e2e": e2e,
                "batch": batch, "serving": serving, "hopper": hopper, "autotune": tuned, "sort_every_step": every,
                "diagnostics": {k: diag[k] for k in ("pair_contacts", "wall_contacts", "max_overlap", "ke_trans")}}
     finally:
