@@ -83,6 +83,9 @@ enum { DEM_TERM_NO_ATTRACTION = 1, DEM_TERM_ROLLING = 2, DEM_TERM_ETA_T = 4, DEM
  *              particle within r_i + r_j + skin is built from the 27 cells and the force
  *              pass reads it instead of walking. K > 1 = as 0, and also at least every K
  *              steps. 0 and K > 1 need skin > 0; they find exactly the same contacts.
+ *              In these modes the library stores each window of block_size consecutive
+ *              (cell, id) positions ordered by the particles' last contact counts, so
+ *              the force kernel's warps get similar amounts of work; results are the same.
  *  block_size  threads per block of the force kernel (32..256); 0 = automatic (256)
  *  terms       optional force terms added to Eqs. 2-10 (none is in the paper; its force
  *              is built from separable terms so that terms can be added, Sec. 3), an OR of:

@@ -55,6 +55,8 @@ struct Domain {
     uint32_t* ncnt = nullptr;
     uint32_t* nl = nullptr;
     float4* ref = nullptr;         // positions at the last sort
+    uint32_t* canon = nullptr;     // (cell, id) position -> pre-sort position, at a sort
+    uint32_t* fin = nullptr;       // (cell, id) position -> stored position (window order by contact count)
 
     // tangential history, double-buffered; h_cur is the buffer the next step reads
     uint32_t* hcnt[2] = {nullptr, nullptr};

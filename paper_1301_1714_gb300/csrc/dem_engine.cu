@@ -93,6 +93,7 @@ void free_particle_buffers(Domain& d) {
     d.S32[0] = d.S32[1] = StateF32{};
     d.ncnt = d.nl = nullptr;
     d.ref = nullptr;
+    d.canon = d.fin = nullptr;
     for (int i = 0; i < 2; ++i) { d.hcnt[i] = nullptr; d.hpid[i] = nullptr; d.hd[i] = nullptr; }
     d.key = d.rank = d.tmp = d.perm = d.skey = d.cnt = d.cs = d.part = nullptr;
     d.diag_part = nullptr;
@@ -299,6 +300,8 @@ dem_status alloc_domain(Domain& d, uint32_t n, uint32_t ncells, std::string& err
         AL(d.ncnt, N * 4);
         AL(d.nl, N * 4 * (size_t)d.maxn);
         AL(d.ref, N * 16);
+        AL(d.canon, N * 4);
+        AL(d.fin, N * 4);
     }
     AL(d.cnt, ((size_t)ccap + 1) * 4);
     AL(d.cs, ((size_t)ccap + 1) * 4);
@@ -1012,8 +1015,17 @@ dem_status dem_debug_snapshot(dem_handle* h, uint32_t* cell, uint32_t* order, in
     CK(h, cudaStreamSynchronize(d.stream));
     if (cell)
         for (size_t q = 0; q < n; ++q) cell[ids[q]] = skey[q];
-    if (order)
-        for (size_t q = 0; q < n; ++q) order[q] = ids[q];
+    if (order) {
+        // storage order; list mode keeps windows ordered by contact count, so the
+        // (cell, id) order is recovered here
+        std::vector<size_t> pos(n);
+        for (size_t q = 0; q < n; ++q) pos[q] = q;
+        if (d.list_mode)
+            std::sort(pos.begin(), pos.end(), [&](size_t a, size_t b) {
+                return skey[a] != skey[b] ? skey[a] < skey[b] : ids[a] < ids[b];
+            });
+        for (size_t q = 0; q < n; ++q) order[q] = ids[pos[q]];
+    }
     if (npairs) *npairs = 0;
     if (pairs || npairs) {
         if (!h->eval_valid) return fail(h, DEM_ERR_STATE, "pairs need a dem_get_forces call on the current state");
@@ -1066,7 +1078,7 @@ int64_t dem_device_bytes(const dem_handle* h) {
     size_t b = 2 * state + 2 * (N * 4 + N * 4 * M + N * T * 3 * M) + 5 * N * 4 + 2 * C * 4 + (size_t)d.part_cap * 4 +
                (size_t)d.diag_part_cap * 80 + sizeof(StatusDev) + 128 + sizeof(SceneDev) * d.scenes_cap;
     b += (size_t)h->stage_cap * (9 * 8 + 4);
-    if (d.list_mode) b += N * (4 + 4 * (size_t)d.maxn + 16);
+    if (d.list_mode) b += N * (4 + 4 * (size_t)d.maxn + 16 + 8);
     return (int64_t)b;
 }
 

@@ -1037,6 +1037,71 @@ __global__ void k_reorder(uint32_t n, typename PR::State S0, typename PR::State 
         reorder_one<PR>(s, A, B, key, cs, tmp, perm, skey, ref);
 }
 
+// List mode stores the sorted particles in (cell, id) order within windows of the force
+// pass's block size, each window ordered by the particles' contact counts in the step
+// just finished (descending; ties keep the (cell, id) order). The lanes of a warp run
+// their candidate lists in lockstep, so grouping similar counts shortens the longest
+// lane's loop; a particle's own sums keep their order, so results do not change.
+// Three passes replace k_reorder: the (cell, id) position of every particle, its final
+// position in its window, and the gather to the final position.
+template <class PR>
+__global__ void k_rank_cell(uint32_t n, typename PR::State S0, typename PR::State S1, const CtrlDev* ctrl,
+                            const uint32_t* __restrict__ key, const uint32_t* __restrict__ cs,
+                            const uint32_t* __restrict__ tmp, const uint32_t* __restrict__ hcnt_last,
+                            uint32_t* __restrict__ canon, uint32_t* __restrict__ wkey) {
+    if (!ctrl->rebuild) return;
+    const typename PR::State B = ctrl->cur ? S0 : S1;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+        const uint32_t p = tmp[s];
+        const uint32_t c = key[p];
+        const uint32_t lo = cs[c], hi = cs[c + 1];
+        const uint32_t idp = B.id[p];
+        uint32_t r = 0;
+        for (uint32_t k = lo; k < hi; ++k) r += (B.id[tmp[k]] < idp) ? 1u : 0u;
+        canon[lo + r] = p;
+        wkey[lo + r] = hcnt_last[p];
+    }
+}
+
+// One block per window of blockDim.x (cell, id) positions: fin[q] = final position.
+__global__ void __launch_bounds__(256) k_window(uint32_t n, const CtrlDev* ctrl, const uint32_t* __restrict__ wkey,
+                                                uint32_t* __restrict__ fin) {
+    if (!ctrl->rebuild) return;
+    __shared__ uint32_t s_key[256];
+    const uint32_t w = blockDim.x;
+    for (uint32_t base = blockIdx.x * w; base < n; base += gridDim.x * w) {
+        const uint32_t q = base + threadIdx.x;
+        const uint32_t key = q < n ? min(wkey[q], 0xFFFFu) : 0u;
+        __syncthreads();
+        s_key[threadIdx.x] = key;
+        __syncthreads();
+        uint32_t rank = 0;
+        for (uint32_t t = 0; t < w; ++t) {
+            const uint32_t kt = s_key[t];
+            rank += (kt > key || (kt == key && t < threadIdx.x)) ? 1u : 0u;
+        }
+        if (q < n) fin[q] = base + rank;
+    }
+}
+
+template <class PR>
+__global__ void k_gather(uint32_t n, typename PR::State S0, typename PR::State S1, const CtrlDev* ctrl,
+                         const uint32_t* __restrict__ key, const uint32_t* __restrict__ canon,
+                         const uint32_t* __restrict__ fin, uint32_t* __restrict__ perm, uint32_t* __restrict__ skey,
+                         float4* __restrict__ ref) {
+    if (!ctrl->rebuild) return;
+    const typename PR::State A = ctrl->cur ? S1 : S0;
+    const typename PR::State B = ctrl->cur ? S0 : S1;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const uint32_t p = canon[q], f = fin[q];
+        const typename PR::Self m = PR::load(B, p);
+        PR::store(A, f, m);
+        perm[f] = p;
+        skey[f] = key[p];
+        ref[f] = PR::pos_f(m);
+    }
+}
+
 // Neighbour lists of the sorted state (list mode): every particle of the 27 cells around
 // each particle (Eq. 12) that lies within r_i + r_j + skin (+ the FP32 margin). With
 // cells of edge >= 2 r_max + skin, no pair that comes into contact before some particle
@@ -1044,8 +1109,9 @@ __global__ void k_reorder(uint32_t n, typename PR::State S0, typename PR::State 
 template <class PR>
 __device__ __forceinline__ uint32_t nlist_one(uint32_t q, const SceneDev* scenes, int nscenes,
                                               const typename PR::State& A, const uint32_t* __restrict__ skey,
-                                              const uint32_t* __restrict__ cs, uint32_t* __restrict__ nl, size_t cap,
-                                              uint32_t maxn, float skin, StatusDev* st) {
+                                              const uint32_t* __restrict__ cs, const uint32_t* __restrict__ fin,
+                                              uint32_t* __restrict__ nl, size_t cap, uint32_t maxn, float skin,
+                                              StatusDev* st) {
     const SceneDev& S = scenes[scene_of(scenes, nscenes, q)];
     const typename PR::Self me = PR::load(A, q);
     const float extra = skin + S.eps_f;
@@ -1068,7 +1134,8 @@ __device__ __forceinline__ uint32_t nlist_one(uint32_t q, const SceneDev* scenes
     uint32_t m = 0;
 #pragma unroll
     for (int r = 0; r < 9; ++r)
-        for (uint32_t j = rlo[r]; j < rhi[r]; ++j) {
+        for (uint32_t jc = rlo[r]; jc < rhi[r]; ++jc) {
+            const uint32_t j = fin[jc];   // the cell table holds (cell, id) positions
             if (j == q || !PR::within(A, me, j, extra)) continue;
             if (m < maxn) nl[m * cap + q] = j;
             ++m;
@@ -1081,12 +1148,13 @@ template <class PR>
 __global__ void __launch_bounds__(256) k_nlist(uint32_t n, const SceneDev* scenes, int nscenes, typename PR::State S0,
                                                 typename PR::State S1, const CtrlDev* ctrl,
                                                 const uint32_t* __restrict__ skey, const uint32_t* __restrict__ cs,
-                                                uint32_t* __restrict__ ncnt, uint32_t* __restrict__ nl, size_t cap,
-                                                uint32_t maxn, float skin, StatusDev* st) {
+                                                const uint32_t* __restrict__ fin, uint32_t* __restrict__ ncnt,
+                                                uint32_t* __restrict__ nl, size_t cap, uint32_t maxn, float skin,
+                                                StatusDev* st) {
     if (!ctrl->rebuild) return;
     const typename PR::State A = ctrl->cur ? S1 : S0;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
-        ncnt[q] = nlist_one<PR>(q, scenes, nscenes, A, skey, cs, nl, cap, maxn, skin, st);
+        ncnt[q] = nlist_one<PR>(q, scenes, nscenes, A, skey, cs, fin, nl, cap, maxn, skin, st);
 }
 
 // Step bookkeeping (one thread): after a sort the current set stays and springs are read
@@ -1358,23 +1426,43 @@ cudaError_t run_rebuild(Domain& d) {
     DEM_LAUNCH_CHECK();
     k_scatter<<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.key, d.rank, d.cs, d.tmp, d.ctrl);
     DEM_LAUNCH_CHECK();
-    float4* ref = d.list_mode ? d.ref : nullptr;
-    if (d.precision == 0)
-        k_reorder<PF64><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.S64[0], d.S64[1], d.ctrl, d.key, d.cs, d.tmp,
-                                                               d.perm, d.skey, ref);
-    else
-        k_reorder<PF32><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.S32[0], d.S32[1], d.ctrl, d.key, d.cs, d.tmp,
-                                                               d.perm, d.skey, ref);
-    DEM_LAUNCH_CHECK();
-    if (d.list_mode) {
+    if (!d.list_mode) {
+        if (d.precision == 0)
+            k_reorder<PF64><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.S64[0], d.S64[1], d.ctrl, d.key, d.cs,
+                                                                   d.tmp, d.perm, d.skey, nullptr);
+        else
+            k_reorder<PF32><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.S32[0], d.S32[1], d.ctrl, d.key, d.cs,
+                                                                   d.tmp, d.perm, d.skey, nullptr);
+        DEM_LAUNCH_CHECK();
+    } else {
+        // (cell, id) positions, the window order by last contact count, the gather
+        const uint32_t* hc = d.hcnt[d.h_cur];   // contact counts of the step just finished (pre-sort order)
+        const uint32_t wb = (uint32_t)d.block;
+        const uint32_t wg = std::max(1u, std::min(nblk(d.n, wb), (uint32_t)std::max(d.sort_blocks, 1)));
+        if (d.precision == 0)
+            k_rank_cell<PF64><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.S64[0], d.S64[1], d.ctrl, d.key, d.cs,
+                                                                     d.tmp, hc, d.canon, d.rank);
+        else
+            k_rank_cell<PF32><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.S32[0], d.S32[1], d.ctrl, d.key, d.cs,
+                                                                     d.tmp, hc, d.canon, d.rank);
+        DEM_LAUNCH_CHECK();
+        k_window<<<wg, wb, 0, d.stream>>>(d.n, d.ctrl, d.rank, d.fin);
+        DEM_LAUNCH_CHECK();
+        if (d.precision == 0)
+            k_gather<PF64><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.S64[0], d.S64[1], d.ctrl, d.key, d.canon,
+                                                                  d.fin, d.perm, d.skey, d.ref);
+        else
+            k_gather<PF32><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.S32[0], d.S32[1], d.ctrl, d.key, d.canon,
+                                                                  d.fin, d.perm, d.skey, d.ref);
+        DEM_LAUNCH_CHECK();
         if (d.precision == 0)
             k_nlist<PF64><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S64[0], d.S64[1], d.ctrl,
-                                                                 d.skey, d.cs, d.ncnt, d.nl, d.cap, (uint32_t)d.maxn,
-                                                                 d.skin_f, d.st);
+                                                                 d.skey, d.cs, d.fin, d.ncnt, d.nl, d.cap,
+                                                                 (uint32_t)d.maxn, d.skin_f, d.st);
         else
             k_nlist<PF32><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S32[0], d.S32[1], d.ctrl,
-                                                                 d.skey, d.cs, d.ncnt, d.nl, d.cap, (uint32_t)d.maxn,
-                                                                 d.skin_f, d.st);
+                                                                 d.skey, d.cs, d.fin, d.ncnt, d.nl, d.cap,
+                                                                 (uint32_t)d.maxn, d.skin_f, d.st);
         DEM_LAUNCH_CHECK();
     }
     return cudaSuccess;

@@ -117,10 +117,10 @@ def test_list_mode_graph_with_conditional_sort_equals_plain_launches(torch_cuda,
     for u, w in zip(a, b):
         assert np.array_equal(u, w)
     assert sa == sb and sa >= 3
-    # plain: 9 kernels per step; graph: force, condition and bookkeeping per step plus the
-    # 7 sort kernels of each sort that ran (the last, odd step runs plain: 9)
-    assert la == 241 * 9
-    assert lb == 240 * 3 + 9 + 7 * sa or lb == 240 * 3 + 9 + 7 * (sa - 1)
+    # plain: 11 kernels per step; graph: force, condition and bookkeeping per step plus
+    # the 9 sort kernels of each sort that ran (the last, odd step runs plain: 11)
+    assert la == 241 * 11
+    assert lb == 240 * 3 + 11 + 9 * sa or lb == 240 * 3 + 11 + 9 * (sa - 1)
 
 
 def test_cancelled_scene_leaves_others_unchanged(torch_cuda):
