@@ -88,10 +88,17 @@ struct StepGraph {
     cudaGraphExec_t exec = nullptr;
     int64_t launches = 0;        // kernels every replay launches
     int64_t body_launches = 0;   // kernels of one conditional sort body (list mode)
+    cudaGraphExec_t sort_exec[2] = {nullptr, nullptr};   // phase timing: the sort tail per history parity
+    int64_t sort_launches = 0;   // kernels every sort-tail replay launches
     cudaStream_t side = nullptr; // stream on which the conditional bodies are captured
     void reset() {
         if (exec) cudaGraphExecDestroy(exec);
         exec = nullptr;
+        for (auto& x : sort_exec) {
+            if (x) cudaGraphExecDestroy(x);
+            x = nullptr;
+        }
+        sort_launches = 0;
         launches = 0;
         body_launches = 0;
         if (side) cudaStreamDestroy(side);

@@ -494,10 +494,10 @@ cudaError_t enqueue_step(Domain& d) {
 // One step for a graph in list mode: force pass, the kernel that sets the condition, a
 // conditional node whose body (captured on the side stream) is the sort and the new
 // lists, then the bookkeeping. A step that does not sort launches three kernels.
-cudaError_t capture_step_cond(Domain& d, StepGraph* g, int64_t& body) {
+// The part of a list-mode step after the force pass, while d.stream is capturing: the
+// condition kernel, the conditional sort node (body captured on g->side), bookkeeping.
+cudaError_t capture_sort_tail(Domain& d, StepGraph* g, int64_t& body) {
     cudaError_t e;
-    if ((e = run_force(d, false, nullptr, nullptr)) != cudaSuccess) return e;
-    d.h_cur = 1 - d.h_cur;
     cudaStreamCaptureStatus cs;
     cudaGraph_t graph = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -535,6 +535,48 @@ cudaError_t capture_step_cond(Domain& d, StepGraph* g, int64_t& body) {
     if (e1 != cudaSuccess) return e1;
     if (e != cudaSuccess) return e;
     return run_end_step(d);
+}
+
+cudaError_t capture_step_cond(Domain& d, StepGraph* g, int64_t& body) {
+    cudaError_t e;
+    if ((e = run_force(d, false, nullptr, nullptr)) != cudaSuccess) return e;
+    d.h_cur = 1 - d.h_cur;
+    return capture_sort_tail(d, g, body);
+}
+
+// Phase timing in list mode: the sort tail of a step as its own graph, one per history
+// parity (the tail reads the contact counts of the buffer the force pass just wrote).
+cudaError_t capture_sort_graphs(Domain& d, StepGraph* g) {
+    cudaError_t e;
+    if (!g->side && (e = cudaStreamCreateWithFlags(&g->side, cudaStreamNonBlocking)) != cudaSuccess) {
+        g->side = nullptr;
+        return e;
+    }
+    const int64_t l0 = d.launches;
+    const int hc0 = d.h_cur;
+    for (int par = 0; par < 2; ++par) {
+        d.h_cur = par;
+        if ((e = cudaStreamBeginCapture(d.stream, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) break;
+        int64_t b = 0;
+        cudaError_t e1 = capture_sort_tail(d, g, b);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(d.stream, &graph);
+        if (e1 == cudaSuccess && e == cudaSuccess) e = cudaGraphInstantiate(&g->sort_exec[par], graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e1 != cudaSuccess) e = e1;
+        if (e != cudaSuccess) break;
+        g->body_launches = b;
+        g->sort_launches = d.launches - l0;
+        d.launches = l0;
+    }
+    d.h_cur = hc0;
+    d.launches = l0;
+    if (e != cudaSuccess) {
+        for (int par = 0; par < 2; ++par)
+            if (g->sort_exec[par]) cudaGraphExecDestroy(g->sort_exec[par]);
+        g->sort_exec[0] = g->sort_exec[1] = nullptr;
+    }
+    return e;
 }
 
 // Two timesteps captured once as a CUDA graph (two, so that the history buffers return
@@ -723,14 +765,23 @@ dem_status dem_step(dem_handle* h, int64_t nsteps) {
         }
     }
     if (timed) {
+        // list mode on a capturable stream: the sort tail runs as a small graph whose sort
+        // node executes only when the device decided to sort
+        if (d.list_mode && d.stream && !h->graph.sort_exec[0] && capture_sort_graphs(d, &h->graph) != cudaSuccess)
+            cudaGetLastError();
         for (int64_t s = 0; s < nsteps; ++s) {
             CK(h, cudaEventRecord(h->events[3 * s], d.stream));
             CK(h, run_force(d, false, nullptr, nullptr));
             CK(h, cudaEventRecord(h->events[3 * s + 1], d.stream));
             d.h_cur = 1 - d.h_cur;
-            if (d.list_mode) CK(h, run_hash(d));   // (sort steps only; fused into the force pass otherwise)
-            CK(h, run_rebuild(d));
-            CK(h, run_end_step(d));
+            if (h->graph.sort_exec[d.h_cur]) {
+                CK(h, cudaGraphLaunch(h->graph.sort_exec[d.h_cur], d.stream));
+                d.launches += h->graph.sort_launches;
+            } else {
+                if (d.list_mode) CK(h, run_hash(d));   // (sort steps only; fused into the force pass otherwise)
+                CK(h, run_rebuild(d));
+                CK(h, run_end_step(d));
+            }
             CK(h, cudaEventRecord(h->events[3 * s + 2], d.stream));
         }
     } else {

@@ -121,6 +121,18 @@ def test_list_mode_graph_with_conditional_sort_equals_plain_launches(torch_cuda,
     # the 9 sort kernels of each sort that ran (the last, odd step runs plain: 11)
     assert la == 241 * 11
     assert lb == 240 * 3 + 11 + 9 * sa or lb == 240 * 3 + 11 + 9 * (sa - 1)
+    # phase timing on a stream: force pass plain, the sort tail as a small graph per step
+    with dem.Simulation(p, sc.x, v, sc.w, sc.r, cuda_stream=stream.cuda_stream) as s:
+        dem.dem_set_timing(s.h, True)
+        l0 = dem.dem_launch_count(s.h)
+        s.step(241)
+        lt = dem.dem_launch_count(s.h) - l0
+        ph = dem.dem_get_phase_times(s.h)
+        c = s.state()
+    for u, w in zip(a, c):
+        assert np.array_equal(u, w)
+    assert lt == 241 * 3 + 9 * sa
+    assert ph[0] > 0 and ph[1] > 0 and ph[2] == 241 and ph[3] == 241
 
 
 def test_cancelled_scene_leaves_others_unchanged(torch_cuda):
