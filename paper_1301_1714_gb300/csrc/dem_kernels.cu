@@ -645,24 +645,14 @@ struct ForceArgs {
     double* dbgT;
 };
 
-// Load the stored tangential spring of partner gid (partner ids are in shared memory).
-// The stored springs are in the order in which the last step met its contacts, and this
-// step meets them in the same order unless a sort intervened, so the search starts after
-// the slot of the previous match (ptr) and wraps around once.
+// Load the stored tangential spring of slot k (partner ids are in shared memory).
 template <class T>
 __device__ __forceinline__ V3<T> find_spring(const uint32_t* s_oid, uint32_t bd, uint32_t tid, uint32_t cnt_old,
-                                             uint32_t gid, const T* hin_d, size_t maxc, size_t cap, uint32_t src,
-                                             uint32_t& ptr) {
-    uint32_t k = ptr;
-    for (uint32_t t = 0; t < cnt_old; ++t) {
-        if (k >= cnt_old) k = 0;
-        if (s_oid[k * bd + tid] == gid) {
-            ptr = k + 1;
+                                             uint32_t gid, const T* hin_d, size_t maxc, size_t cap, uint32_t src) {
+    for (uint32_t k = 0; k < cnt_old; ++k)
+        if (s_oid[k * bd + tid] == gid)
             return mk(hin_d[(0 * maxc + k) * cap + src], hin_d[(1 * maxc + k) * cap + src],
                       hin_d[(2 * maxc + k) * cap + src]);
-        }
-        ++k;
-    }
     return mk(T(0), T(0), T(0));
 }
 
@@ -774,7 +764,6 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
         mi = PR::mass(S, me.r);
     }
     uint64_t mask_left = near_mask;
-    uint32_t sptr = 0;                    // slot after the last matched stored spring
     for (uint32_t k = 0; k < kmax; ++k) {
         if (!(live && k < mylen)) continue;
         uint32_t j;
@@ -801,7 +790,7 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
             const T mj = PR::mass(S, rj);
             const T meff = law_div(mi * mj, mi + mj);
             const T Reff = law_div(ri * rjT, ri + rjT);
-            const V3<T> dold = find_spring(s_oid, bd, tid, cnt_old, gid, a.hin_d, (size_t)maxc, cap, src, sptr);
+            const V3<T> dold = find_spring(s_oid, bd, tid, cnt_old, gid, a.hin_d, (size_t)maxc, cap, src);
             V3<T> Fc, Ftc, dnew, Mr;
             law_practical<TERMS>(L, n, delta, v, rw, Reff, meff, dold, Fc, Ftc, dnew, me.w - wj, Mr);
             F = F + Fc;
@@ -832,7 +821,7 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
             const uint32_t gid = DEM_WALL_BASE + (uint32_t)w;
             if (PRACT) {
                 const V3<T> rw = me.w * ri;
-                const V3<T> dold = find_spring(s_oid, bd, tid, cnt_old, gid, a.hin_d, (size_t)maxc, cap, src, sptr);
+                const V3<T> dold = find_spring(s_oid, bd, tid, cnt_old, gid, a.hin_d, (size_t)maxc, cap, src);
                 V3<T> Fc, Ftc, dnew, Mr;
                 law_practical<TERMS>(L, n, delta, v, rw, ri, mi, dold, Fc, Ftc, dnew, me.w - PR::wall_omega(W), Mr);
                 F = F + Fc;
