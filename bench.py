@@ -89,13 +89,16 @@ def make_scene(args, rank=0):
     return scenes.box_lattice(seed=seed, precision="fp64")
 
 
-def workload_desc(args, sc, p=None):
+def workload_desc(args, sc, p=None, impl="ours"):
     p = p or sc.params
     if args.workload == "drum":
+        base = (f"drum: {sc.n:,} spheres r~U[0.9,1.1] mm, drum R=300r L=208r rotating 2 rad/s, mu={p.mu}, e=0.7, "
+                f"practical linear kn={p.kn:g} N/m, dt={p.dt:.5e} s")
+        if impl == "reference":
+            return base + ", FP64 oracle: every step's pairs from the cell grid"
         sort = ("sort every step" if p.resort_interval == 1 else
                 f"sort when a particle moved skin/2 (skin {p.skin * 1e3:.2f} mm), neighbour lists")
-        return (f"drum: {sc.n:,} spheres r~U[0.9,1.1] mm, drum R=300r L=208r rotating 2 rad/s, mu={p.mu}, e=0.7, "
-                f"practical linear kn={p.kn:g} N/m, dt={p.dt:.5e} s, FP32 forces + compensated positions, {sort}")
+        return base + f", FP32 forces + compensated positions, {sort}"
     if args.workload == "rsa":
         return f"box settling: {sc.n:,} spheres r~U[0.8,1.2] mm, RSA loose fill, practical linear, FP32"
     return f"box: {sc.n:,} spheres r=1 mm, jittered lattice, practical linear, FP64"
@@ -628,7 +631,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": round(dt * 1e3 / args.steps, 3),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": workload_desc(args, sc), "n_particles": sc.n, "seed": args.seed},
+           "config": {"workload": workload_desc(args, sc, impl="reference"), "n_particles": sc.n, "seed": args.seed},
            "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc},
            "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
