@@ -316,24 +316,17 @@ struct PF32 {
         const float eps = S.eps_f;
         uint64_t mask = 0;
         uint32_t k = 0;
+        // (no L1 prefetch of the near candidates' payload here: measured 9% slower, the
+        // prefetched lines are evicted before phase 2 reads them)
         for (; k + 2 <= m; k += 2) {
             const uint32_t j0 = __ldg(&nl[k * cap + q]), j1 = __ldg(&nl[(k + 1) * cap + q]);
             const float4 a = __ldg(&s.P0[j0]), b = __ldg(&s.P0[j1]);
-            if (near(me, a, eps)) {
-                mask |= 1ull << k;
-                prefetch_partner(s, j0);
-            }
-            if (near(me, b, eps)) {
-                mask |= 1ull << (k + 1);
-                prefetch_partner(s, j1);
-            }
+            if (near(me, a, eps)) mask |= 1ull << k;
+            if (near(me, b, eps)) mask |= 1ull << (k + 1);
         }
         if (k < m) {
             const uint32_t j0 = __ldg(&nl[k * cap + q]);
-            if (near(me, __ldg(&s.P0[j0]), eps)) {
-                mask |= 1ull << k;
-                prefetch_partner(s, j0);
-            }
+            if (near(me, __ldg(&s.P0[j0]), eps)) mask |= 1ull << k;
         }
         return mask;
     }
