@@ -105,10 +105,6 @@ struct PF64 {
     static __device__ __forceinline__ float4 pos_f(const Self& m) {
         return make_float4((float)m.x, (float)m.y, (float)m.z, 0.f);
     }
-    static __device__ __forceinline__ void prefetch_partner(const State& s, uint32_t j) {
-        prefetch_l1(&s.vx[j]);
-        prefetch_l1(&s.wx[j]);
-    }
     struct Partner {
         uint32_t j;
         uint32_t id;
@@ -316,8 +312,8 @@ struct PF32 {
         const float eps = S.eps_f;
         uint64_t mask = 0;
         uint32_t k = 0;
-        // (no L1 prefetch of the near candidates' payload here: measured 9% slower, the
-        // prefetched lines are evicted before phase 2 reads them)
+        // (no L1 prefetch of the near candidates' payload: measured 9% slower here and 4%
+        // in the walk; the prefetched lines are evicted before phase 2 reads them)
         for (; k + 2 <= m; k += 2) {
             const uint32_t j0 = __ldg(&nl[k * cap + q]), j1 = __ldg(&nl[(k + 1) * cap + q]);
             const float4 a = __ldg(&s.P0[j0]), b = __ldg(&s.P0[j1]);
@@ -339,12 +335,6 @@ struct PF32 {
         return ax * ax + ay * ay + az * az < Re * Re;
     }
     static __device__ __forceinline__ float4 pos_f(const Self& m) { return make_float4(m.hx, m.hy, m.hz, 0.f); }
-    // payload that phase 2 reads for a listed candidate
-    static __device__ __forceinline__ void prefetch_partner(const State& s, uint32_t j) {
-        prefetch_l1(&s.P1[j]);
-        prefetch_l1(&s.V[j]);
-        prefetch_l1(&s.W[j]);
-    }
     // Everything phase 2 reads of a candidate, loaded together so the latencies overlap.
     struct Partner {
         float4 p0, p1, v, w;
@@ -744,8 +734,6 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
     }
     // ---- phase 2: contacts, in lockstep over the lists
     const uint32_t mylen = LIST ? nnear : min(nnear, maxc);
-    if (live && !LIST)
-        for (uint32_t k = 0; k < mylen; ++k) PR::prefetch_partner(A, s_near[k * bd + tid]);
     const uint32_t kmax = __reduce_max_sync(0xffffffffu, mylen);
     V3<T> F = mk(T(0), T(0), T(0)), Tq = mk(T(0), T(0), T(0));
     uint32_t nnew = 0;
