@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--skin-r", type=float, default=0.1, help="skin in largest radii (used when --resort is 0 or K)")
     ap.add_argument("--max-contacts", type=int, default=0, help="per-particle contact capacity (0 = library default)")
     ap.add_argument("--block", type=int, default=0, help="force-kernel block size when not autotuned (0 = default)")
+    ap.add_argument("--legacy-stream", action="store_true",
+                    help="run the timed handle on the legacy default stream: every kernel is launched on its own "
+                         "(no step graphs), for per-kernel launch lists")
     ap.add_argument("--simple-steps", type=int, default=500)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -427,7 +430,8 @@ def run_ours(args):
         p = sc.params if k == 1 else sc.params.copy(resort_interval=k, skin=args.skin_r * rmax,
                                                     cell_size=sc.params.cell_size + args.skin_r * rmax)
     cfg = dem.config_from_params(p, block_size=block, max_contacts=args.max_contacts)
-    h = dem.dem_create(cfg, dev.index, stream.cuda_stream)
+    h = dem.dem_create(cfg, dev.index, None if args.legacy_stream else stream.cuda_stream)
+    tstream = torch.cuda.default_stream(dev) if args.legacy_stream else stream   # the timed handle's stream
     try:
         dem.dem_set_walls(h, p.walls)
         dem.dem_set_particles(h, xs0, vs0, ws0, sc.r)
@@ -445,9 +449,9 @@ def run_ours(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         nvtx_push("timed")                            # lets a profiler select the timed steps
-        e0.record(stream)
+        e0.record(tstream)
         dem.dem_step(h, args.steps)
-        e1.record(stream)
+        e1.record(tstream)
         torch.cuda.synchronize(dev)
         nvtx_pop()
         clocks = clk.stop()
@@ -465,9 +469,9 @@ def run_ours(args):
         lg0 = dem.dem_launch_count(h)
         g0 = torch.cuda.Event(enable_timing=True)
         g1 = torch.cuda.Event(enable_timing=True)
-        g0.record(stream)
+        g0.record(tstream)
         dem.dem_step(h, args.steps)
-        g1.record(stream)
+        g1.record(tstream)
         torch.cuda.synchronize(dev)
         ms_graph = replicas.reduce_max(g0.elapsed_time(g1), dev)
         graph = {"value": round(replicas.reduce_sum(float(N), dev) * args.steps / (ms_graph / 1e3), 1),
