@@ -174,12 +174,13 @@ def run_batch_bench(args, dem, dev_index, stream):
             "batched_over_sequential": round(batched / seq, 2) if seq else None}
 
 
-def run_hopper_bench(args, dem, dev_index, stream):
+def run_hopper_bench(args, dem, dev_index, stream, block=0):
     """The paper's benchmark shape (Sec. 5, Table 3): 131,072 equal spheres in a box drain
     through a slit in its bottom onto a floor. The box is filled at rest with the bottom
     closed (accelerated settling), the slit opens, the flow runs `hopper_drain` steps, then
     the practical and the simple model are each timed for `hopper_steps` steps from that
-    state (FP32, skin-driven sorting), and the FP64 oracle on a bounded slab of it."""
+    state (FP32, skin-driven sorting, the drum's tuned block size), and the FP64 oracle on
+    a bounded slab of it."""
     import torch
     from paper_1301_1714_gb300 import scenes
     closed = scenes.hopper(seed=args.seed, open_slit=False)
@@ -193,7 +194,7 @@ def run_hopper_bench(args, dem, dev_index, stream):
            "n_particles": N, "steps": args.hopper_steps}
     for model in ("practical", "simple"):
         p = opened.params.copy(model=model, resort_interval=0, skin=skin, cell_size=opened.params.cell_size + skin)
-        h = dem.dem_create(dem.config_from_params(p), dev_index, stream.cuda_stream)
+        h = dem.dem_create(dem.config_from_params(p, block_size=block), dev_index, stream.cuda_stream)
         try:
             dem.dem_set_walls(h, p.walls)
             dem.dem_set_particles(h, x, v, w, closed.r)
@@ -577,7 +578,7 @@ def run_ours(args):
 
         batch = run_batch_bench(args, dem, dev.index, stream) if args.batch_scenes > 0 else None
         serving = run_serve_bench(args, dem, dev.index, stream) if args.serve_requests > 0 else None
-        hopper = (run_hopper_bench(args, dem, dev.index, stream)
+        hopper = (run_hopper_bench(args, dem, dev.index, stream, block)
                   if args.hopper_steps > 0 and rank == 0 and world == 1 else None)
         out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,

@@ -253,7 +253,7 @@ struct PF32 {
     };
     static __device__ __forceinline__ Self load(const State& s, uint32_t q) {
         Self m;
-        const float4 p0 = s.P0[q], p1 = s.P1[q], v = s.V[q], w = s.W[q];
+        const float4 p0 = __ldg(&s.P0[q]), p1 = __ldg(&s.P1[q]), v = __ldg(&s.V[q]), w = __ldg(&s.W[q]);
         m.hx = p0.x; m.hy = p0.y; m.hz = p0.z; m.r = p0.w;
         m.lx = p1.x; m.ly = p1.y; m.lz = p1.z;
         m.v = mk(v.x, v.y, v.z);
@@ -634,8 +634,8 @@ __device__ __forceinline__ V3<T> find_spring(const uint32_t* s_oid, uint32_t bd,
                                              uint32_t gid, const T* hin_d, size_t maxc, size_t cap, uint32_t src) {
     for (uint32_t k = 0; k < cnt_old; ++k)
         if (s_oid[k * bd + tid] == gid)
-            return mk(hin_d[(0 * maxc + k) * cap + src], hin_d[(1 * maxc + k) * cap + src],
-                      hin_d[(2 * maxc + k) * cap + src]);
+            return mk(__ldg(&hin_d[(0 * maxc + k) * cap + src]), __ldg(&hin_d[(1 * maxc + k) * cap + src]),
+                      __ldg(&hin_d[(2 * maxc + k) * cap + src]));
     return mk(T(0), T(0), T(0));
 }
 
@@ -676,14 +676,14 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
     uint32_t src = 0, cnt_old = 0, nnear = 0;
     if (valid) {
         me = PR::load(A, q);
-        src = pv ? a.perm[q] : q;
+        src = pv ? __ldg(&a.perm[q]) : q;
         if (PRACT || !S.active) {
-            cnt_old = min(a.hin_cnt[src], maxc);
+            cnt_old = min(__ldg(&a.hin_cnt[src]), maxc);
             // the stored springs are streamed from DRAM: start their loads now so they are
             // in L1 when phase 2 matches contacts against them
             for (uint32_t k = 0; k < cnt_old; ++k)
                 for (int c = 0; c < 3; ++c) prefetch_l1(&a.hin_d[(c * (size_t)maxc + k) * cap + src]);
-            for (uint32_t k = 0; k < cnt_old; ++k) s_oid[k * bd + tid] = a.hin_pid[k * cap + src];
+            for (uint32_t k = 0; k < cnt_old; ++k) s_oid[k * bd + tid] = __ldg(&a.hin_pid[k * cap + src]);
         }
     }
     if (valid && !live) {
