@@ -13,7 +13,6 @@
 //   k_import / k_export / k_diag* / k_hist_canon / k_repack   set-up, read-out,
 //                diagnostics, batch repacking
 #include <algorithm>
-#include <type_traits>
 
 #include <cuda_runtime.h>
 
@@ -640,137 +639,6 @@ __device__ __forceinline__ V3<T> find_spring(const uint32_t* s_oid, uint32_t bd,
     return mk(T(0), T(0), T(0));
 }
 
-// List-mode contact phase in FP32 mode, dealt out over the warp: the near candidates of
-// the warp's 32 particles are numbered in (lane, list) order and processed 32 at a time,
-// one per lane, so the lanes stay busy however unevenly the contacts fall. A lane reads
-// the owning particle's state from shared memory (staged by its owner), evaluates the
-// contact and its spring, and leaves the force and torque in shared memory; each owner
-// then adds its own contacts in list order, so every particle's sums have the same
-// order (and bits) as when it evaluates its contacts itself. Spring slots follow the
-// contacts' order per owner.
-constexpr int OWN_WORDS = 17;   // staged per particle: hi(3) lo(3) r v(3) w(3) m src cnt_old id
-constexpr int RES_WORDS = 6;    // per item: force(3) torque(3)
-
-template <int MODEL, bool EVAL>
-__device__ __forceinline__ void contacts_dealt(const ForceArgs<PF32>& a, const StateF32& A, const SceneDev& S,
-                                               const Law<float>& L, bool live, uint64_t near_mask, uint32_t q,
-                                               uint32_t tid, uint32_t bd, uint32_t maxc, size_t cap,
-                                               const uint32_t* s_oid, float* s_own, float* s_res, V3<float>& F,
-                                               V3<float>& Tq, uint32_t& nnew, uint32_t& c_pp, float& c_maxov) {
-    constexpr bool PRACT = MODEL != 1;
-    constexpr bool TERMS = MODEL == 2;
-    const unsigned full = 0xffffffffu;
-    const uint32_t lane = tid & 31u, wbase = tid & ~31u;
-    const uint32_t cnt = live ? (uint32_t)__popcll(near_mask) : 0u;
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t t = __shfl_up_sync(full, incl, off);
-        if (lane >= (uint32_t)off) incl += t;
-    }
-    const uint32_t excl = incl - cnt;
-    const uint32_t total = __shfl_sync(full, incl, 31);
-    const uint32_t lo_mask = (uint32_t)near_mask, hi_mask = (uint32_t)(near_mask >> 32);
-    __syncwarp();
-    for (uint32_t base = 0; base < total; base += 32) {
-        const uint32_t t = base + lane;
-        const bool act = t < total;
-        // owner: the last lane whose first item is at or before t
-        uint32_t o = 0;
-#pragma unroll
-        for (uint32_t step = 16; step >= 1; step >>= 1) {
-            const uint32_t ex = __shfl_sync(full, excl, o + step);
-            if (ex <= t) o += step;
-        }
-        const uint32_t ml = __shfl_sync(full, lo_mask, o), mh = __shfl_sync(full, hi_mask, o);
-        const uint32_t idx = t - __shfl_sync(full, excl, o);
-        bool contact = false;
-        float delta = 0.f;
-        uint32_t gid = 0;
-        V3<float> Fc = mk(0.f, 0.f, 0.f), Tc = mk(0.f, 0.f, 0.f), dnew = mk(0.f, 0.f, 0.f);
-        const uint32_t to = wbase + o;                 // owner's thread in the block
-        const uint32_t qo = q - tid + to;              // owner's particle
-        if (act) {
-            // list entry of the owner's idx-th near candidate
-            uint64_t m = ((uint64_t)mh << 32) | ml;
-            for (uint32_t i = 0; i < idx && i < 64; ++i) m &= m - 1;
-            const int e = __ffsll((long long)m) - 1;
-            if (e >= 0) {
-                const uint32_t j = __ldg(&a.nl[(size_t)e * cap + qo]);
-                PF32::Self me;
-                me.hx = s_own[0 * bd + to]; me.hy = s_own[1 * bd + to]; me.hz = s_own[2 * bd + to];
-                me.lx = s_own[3 * bd + to]; me.ly = s_own[4 * bd + to]; me.lz = s_own[5 * bd + to];
-                me.r = s_own[6 * bd + to];
-                me.v = mk(s_own[7 * bd + to], s_own[8 * bd + to], s_own[9 * bd + to]);
-                me.w = mk(s_own[10 * bd + to], s_own[11 * bd + to], s_own[12 * bd + to]);
-                me.id = 0;
-                const float mi = s_own[13 * bd + to];
-                const float ri = me.r;
-                V3<float> n;
-                float rj;
-                const PF32::Partner pj = PF32::load_partner(A, j);
-                if (PF32::exact_p(A, pj, me, n, delta, rj)) {
-                    contact = true;
-                    gid = pj.id;
-                    V3<float> vj, wj;
-                    PF32::partner_vw(pj, vj, wj);
-                    const V3<float> v = me.v - vj;
-                    if (PRACT) {
-                        const V3<float> rw = mk(sym_madd(ri, me.w.x, rj, wj.x), sym_madd(ri, me.w.y, rj, wj.y),
-                                                sym_madd(ri, me.w.z, rj, wj.z));
-                        const float mj = PF32::mass(S, rj);
-                        const float meff = law_div(mi * mj, mi + mj);
-                        const float Reff = law_div(ri * rj, ri + rj);
-                        const uint32_t src = __float_as_uint(s_own[14 * bd + to]);
-                        const uint32_t cnt_old = __float_as_uint(s_own[15 * bd + to]);
-                        const V3<float> dold =
-                            find_spring(s_oid, bd, to, cnt_old, gid, a.hin_d, (size_t)maxc, cap, src);
-                        V3<float> Ftc, Mr;
-                        law_practical<TERMS>(L, n, delta, v, rw, Reff, meff, dold, Fc, Ftc, dnew, me.w - wj, Mr);
-                        Tc = cross(n, Ftc) * ri;
-                        if (TERMS) Tc = Tc + Mr;
-                    } else {
-                        Fc = law_simple(L, n, delta, v);
-                    }
-                }
-            }
-        }
-        const uint32_t M = __ballot_sync(full, contact);
-        const uint32_t peers = __match_any_sync(full, act ? o : 64u + lane);
-        const uint32_t before = __shfl_sync(full, nnew, o);
-        if (contact) {
-            const uint32_t slot = before + (uint32_t)__popc(M & peers & ((1u << lane) - 1u));
-            if (slot < maxc) {
-                if (PRACT) {
-                    a.hout_pid[slot * cap + qo] = gid;
-                    a.hout_d[(0 * (size_t)maxc + slot) * cap + qo] = dnew.x;
-                    a.hout_d[(1 * (size_t)maxc + slot) * cap + qo] = dnew.y;
-                    a.hout_d[(2 * (size_t)maxc + slot) * cap + qo] = dnew.z;
-                } else if (EVAL) {
-                    a.hout_pid[slot * cap + qo] = gid;
-                }
-            }
-            s_res[0 * bd + tid] = Fc.x; s_res[1 * bd + tid] = Fc.y; s_res[2 * bd + tid] = Fc.z;
-            s_res[3 * bd + tid] = Tc.x; s_res[4 * bd + tid] = Tc.y; s_res[5 * bd + tid] = Tc.z;
-            ++c_pp;
-            c_maxov = fmaxf(c_maxov, delta);
-        }
-        __syncwarp();
-        // the owner adds its contacts of this round, in item order
-        const uint32_t a0 = max(excl, base), a1 = min(excl + cnt, base + 32);
-        for (uint32_t t2 = a0; t2 < a1; ++t2) {
-            const uint32_t l2 = t2 - base;
-            if ((M >> l2) & 1u) {
-                const uint32_t r2 = wbase + l2;
-                F = F + mk(s_res[0 * bd + r2], s_res[1 * bd + r2], s_res[2 * bd + r2]);
-                Tq = Tq + mk(s_res[3 * bd + r2], s_res[4 * bd + r2], s_res[5 * bd + r2]);
-                ++nnew;
-            }
-        }
-        __syncwarp();
-    }
-}
-
 // One thread per cell-sorted particle. Phase 1 walks the 27 cells (Eq. 12) as 9 rows of
 // three x-adjacent cells and keeps the candidates that may touch in a per-thread list in
 // shared memory; phase 2 runs the lanes of a warp in lockstep over their lists (the warp
@@ -877,38 +745,7 @@ __global__ void __launch_bounds__(256, LIST ? DEM_FORCE_MIN_BLOCKS_LIST : DEM_FO
         mi = PR::mass(S, me.r);
     }
     uint64_t mask_left = near_mask;
-    if constexpr (LIST && std::is_same<PR, PF32>::value) {
-        // stage this particle for the lanes that evaluate its contacts, then deal them out
-        float* s_own = reinterpret_cast<float*>(smem + maxc * bd);
-        float* s_res = s_own + OWN_WORDS * bd;
-        if (live) {
-            s_own[0 * bd + tid] = me.hx; s_own[1 * bd + tid] = me.hy; s_own[2 * bd + tid] = me.hz;
-            s_own[3 * bd + tid] = me.lx; s_own[4 * bd + tid] = me.ly; s_own[5 * bd + tid] = me.lz;
-            s_own[6 * bd + tid] = me.r;
-            s_own[7 * bd + tid] = me.v.x; s_own[8 * bd + tid] = me.v.y; s_own[9 * bd + tid] = me.v.z;
-            s_own[10 * bd + tid] = me.w.x; s_own[11 * bd + tid] = me.w.y; s_own[12 * bd + tid] = me.w.z;
-            s_own[13 * bd + tid] = mi;
-            s_own[14 * bd + tid] = __uint_as_float(src);
-            s_own[15 * bd + tid] = __uint_as_float(cnt_old);
-            s_own[16 * bd + tid] = __uint_as_float(me.id);
-        }
-        contacts_dealt<MODEL, EVAL>(a, A, S, L, live, near_mask, q, tid, bd, maxc, cap, s_oid, s_own, s_res, F, Tq,
-                                    nnew, c_pp, c_maxov);
-        // the particle's own state back from shared memory (not held in registers meanwhile)
-        if (live) {
-            me.hx = s_own[0 * bd + tid]; me.hy = s_own[1 * bd + tid]; me.hz = s_own[2 * bd + tid];
-            me.lx = s_own[3 * bd + tid]; me.ly = s_own[4 * bd + tid]; me.lz = s_own[5 * bd + tid];
-            me.r = s_own[6 * bd + tid];
-            me.v = mk(s_own[7 * bd + tid], s_own[8 * bd + tid], s_own[9 * bd + tid]);
-            me.w = mk(s_own[10 * bd + tid], s_own[11 * bd + tid], s_own[12 * bd + tid]);
-            mi = s_own[13 * bd + tid];
-            src = __float_as_uint(s_own[14 * bd + tid]);
-            cnt_old = __float_as_uint(s_own[15 * bd + tid]);
-            me.id = __float_as_uint(s_own[16 * bd + tid]);
-        }
-    }
     for (uint32_t k = 0; k < kmax; ++k) {
-        if constexpr (LIST && std::is_same<PR, PF32>::value) break;
         if (!(live && k < mylen)) continue;
         uint32_t j;
         if (LIST) {
@@ -1667,10 +1504,7 @@ static cudaError_t force_impl(Domain& d, const typename PR::State& S0, const typ
     a.dbgF = dbgF;
     a.dbgT = dbgT;
     const uint32_t b = (uint32_t)d.block;
-    // list mode (FP32) also stages each particle and each dealt contact's result
-    const size_t words = d.list_mode ? (size_t)d.maxc + (d.precision == 1 ? OWN_WORDS + RES_WORDS : 0)
-                                     : 2 * (size_t)d.maxc;
-    const size_t smem = words * b * sizeof(uint32_t);
+    const size_t smem = (d.list_mode ? 1 : 2) * (size_t)d.maxc * b * sizeof(uint32_t);
     const uint32_t g = nblk(d.n, b);
     auto launch = [&](auto kern) -> cudaError_t {
         // lists of 2 x maxc ids per thread may exceed the 48 KB default of dynamic shared memory
