@@ -15,7 +15,7 @@ from . import dem
 # (block size, resort_interval, skin as a fraction of the largest radius)
 DEFAULT_CANDIDATES: Tuple[Tuple[int, int, float], ...] = (
     (256, 1, 0.0), (128, 1, 0.0),
-    (256, 0, 0.05), (256, 0, 0.1), (256, 0, 0.2), (128, 0, 0.1),
+    (256, 0, 0.1), (128, 0, 0.05), (128, 0, 0.1), (128, 0, 0.15), (128, 0, 0.2), (96, 0, 0.1),
 )
 
 
