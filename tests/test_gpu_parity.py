@@ -499,6 +499,29 @@ def test_list_mode_drum_matches_oracle(precision):
     assert d["sorts"] >= 120 // 25
 
 
+@pytest.mark.parametrize("model,stiff", [("practical", "hertz"), ("simple", "linear")])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_list_mode_other_laws_match_oracle(model, stiff, precision):
+    """Neighbour lists with the Hertz law (Eqs. 8-9) and with the simple law (Eq. 1)."""
+    sc = scenes.box_lattice(seed=4, stiffness=stiff, model=model)
+    base = sc.params
+    p = listed(base.copy(precision=precision))
+    ref = oracle.State(base, sc.x, sc.v, sc.w, sc.r)
+    with sim(p, sc) as s:
+        s.step(10)
+        x10, _, _ = s.state()
+        ref.run(10)
+        if precision == "fp64":
+            assert np.max(np.abs(x10 - ref.x)) <= 1e-12
+        s.step(290)
+        x, _, _ = s.state()
+        d = s.diagnostics()
+    ref.run(290)
+    disp = np.max(np.linalg.norm(ref.x - sc.x, axis=1))
+    assert np.max(np.abs(x - ref.x)) <= (1e-9 if precision == "fp64" else 1e-5 * disp)
+    assert d["pair_contacts"] + d["wall_contacts"] > 0
+
+
 def test_list_mode_pairs_equal_sort_every_step_pairs():
     """After many list-mode steps, the contact pairs found through the lists equal those
     found by a fresh 27-cell walk of the same state (GPU against GPU)."""
