@@ -97,6 +97,9 @@ def test_full_hopper_forces_match_oracle():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA GPU")
+    from paper_1301_1714_gb300 import _build
+    _build.build()
+    dem.lib()
     sc = scenes.hopper(seed=2)
     x = sc.x.copy()
     x[:, 2] -= 0.12e-3
