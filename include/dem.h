@@ -301,6 +301,11 @@ dem_status dem_sort_cells_static(int64_t n, const double* x, const double* origi
 /* Bytes of device memory held by the handle. */
 int64_t dem_device_bytes(const dem_handle* h);
 
+/* Largest number of contacts (particles and walls) of any one particle in the last
+ * step, as read at the end of the last dem_step; dem_config.max_contacts must stay
+ * above it (a step that exceeds the capacity fails with DEM_ERR_CAPACITY). */
+int64_t dem_max_contacts_seen(const dem_handle* h);
+
 /* Number of kernel launches the handle has enqueued so far (kernels that a replayed step
  * graph ran conditionally are counted from a device-side counter: the call synchronises
  * the handle's stream). */

@@ -37,13 +37,13 @@ def apply(params, rmax: float, choice: Choice):
 
 
 def tune(params, x, v, w, r, candidates: Sequence[Tuple[int, int, float]] = DEFAULT_CANDIDATES, steps: int = 60,
-         warmup: int = 20, device: int = 0, cuda_stream=None) -> Tuple[Choice, List[Choice]]:
+         warmup: int = 20, device: int = 0, cuda_stream=None, max_contacts: int = 0) -> Tuple[Choice, List[Choice]]:
     rmax = float(max(r)) if len(r) else 1.0
     table: List[Choice] = []
     for block, resort, sk in candidates:
         c = Choice(block, resort, sk, 0.0, 0.0, 0.0)
         p = apply(params, rmax, c)
-        h = dem.dem_create(dem.config_from_params(p, block_size=block), device, cuda_stream)
+        h = dem.dem_create(dem.config_from_params(p, block_size=block, max_contacts=max_contacts), device, cuda_stream)
         try:
             dem.dem_set_walls(h, p.walls)
             dem.dem_set_particles(h, x, v, w, r)

@@ -1133,6 +1133,10 @@ int64_t dem_device_bytes(const dem_handle* h) {
     return (int64_t)b;
 }
 
+int64_t dem_max_contacts_seen(const dem_handle* h) {
+    return (h && h->d.st_host) ? (int64_t)h->d.st_host->last.max_nnew : 0;
+}
+
 int64_t dem_launch_count(const dem_handle* h) {
     if (!h) return 0;
     int64_t n = h->d.launches;

@@ -54,7 +54,8 @@ class DemError(RuntimeError):
 _lib = None
 _EXPORTS = ["dem_create", "dem_set_particles", "dem_set_walls", "dem_step", "dem_run_until", "dem_get_state", "dem_get_forces",
             "dem_get_history", "dem_restore", "dem_get_diagnostics", "dem_debug_snapshot", "dem_get_grid",
-            "dem_device_bytes", "dem_launch_count", "dem_last_error", "dem_destroy", "dem_set_timing",
+            "dem_device_bytes", "dem_max_contacts_seen", "dem_launch_count", "dem_last_error", "dem_destroy",
+            "dem_set_timing",
             "dem_get_phase_times", "dem_sort_cells_static", "dem_batch_create", "dem_batch_add", "dem_batch_run",
             "dem_batch_get_state", "dem_batch_remove", "dem_batch_info", "dem_batch_device_bytes",
             "dem_batch_launch_count", "dem_batch_last_error", "dem_batch_destroy"]
@@ -106,6 +107,8 @@ def lib():
     L.dem_get_phase_times.argtypes = [P, P]
     L.dem_device_bytes.argtypes = [P]
     L.dem_device_bytes.restype = I64
+    L.dem_max_contacts_seen.argtypes = [P]
+    L.dem_max_contacts_seen.restype = I64
     L.dem_launch_count.argtypes = [P]
     L.dem_launch_count.restype = I64
     L.dem_last_error.argtypes = [P]
@@ -342,6 +345,10 @@ def dem_get_phase_times(h):
 
 def dem_device_bytes(h):
     return int(lib().dem_device_bytes(h))
+
+
+def dem_max_contacts_seen(h):
+    return int(lib().dem_max_contacts_seen(h))
 
 
 def dem_launch_count(h):

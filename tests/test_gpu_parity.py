@@ -388,6 +388,24 @@ def test_list_mode_block_size_does_not_change_results(block):
     assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(wa, wb)
 
 
+@pytest.mark.parametrize("list_mode", [False, True])
+def test_max_contacts_seen_counts_pairs_and_walls(list_mode):
+    """dem_max_contacts_seen after one step = the largest per-particle count of contact
+    partners (particles and walls) at the state the step started from."""
+    sc = scenes.box_lattice(seed=1)
+    x = compressed(sc, SQUEEZE["box2048"])
+    p = listed(sc.params) if list_mode else sc.params
+    pairs = oracle.pairs_brute(x, sc.r)
+    cnt = np.bincount(pairs.ravel(), minlength=sc.n)
+    for wl in sc.params.walls:
+        s_ = (x - np.array(wl["p"])) @ np.array(wl["n"])
+        cnt += (s_ < sc.r.astype(np.float64)).astype(np.int64)
+    with dem.Simulation(p, x, sc.v, sc.w, sc.r) as s:
+        s.step(1)
+        seen = dem.dem_max_contacts_seen(s.h)
+    assert seen == cnt.max() and seen > 3
+
+
 def test_capacity_overflow_is_reported():
     sc = scenes.box_lattice(seed=1)
     x = compressed(sc, 0.95)
