@@ -520,7 +520,10 @@ def test_list_mode_drum_matches_oracle(precision):
 @pytest.mark.parametrize("model,stiff", [("practical", "hertz"), ("simple", "linear")])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_list_mode_other_laws_match_oracle(model, stiff, precision):
-    """Neighbour lists with the Hertz law (Eqs. 8-9) and with the simple law (Eq. 1)."""
+    """Neighbour lists with the Hertz law (Eqs. 8-9) and with the simple law (Eq. 1):
+    FP64 follows the oracle to 1e-12 m after 10 steps and 1e-9 m after 300; FP32 stays
+    as close to the oracle as the sort-every-step FP32 run (whose difference from the
+    oracle is FP32 rounding amplified by the collisions)."""
     sc = scenes.box_lattice(seed=4, stiffness=stiff, model=model)
     base = sc.params
     p = listed(base.copy(precision=precision))
@@ -535,8 +538,16 @@ def test_list_mode_other_laws_match_oracle(model, stiff, precision):
         x, _, _ = s.state()
         d = s.diagnostics()
     ref.run(290)
-    disp = np.max(np.linalg.norm(ref.x - sc.x, axis=1))
-    assert np.max(np.abs(x - ref.x)) <= (1e-9 if precision == "fp64" else 1e-5 * disp)
+    err = np.max(np.abs(x - ref.x))
+    if precision == "fp64":
+        assert err <= 1e-9
+    else:
+        with sim(base.copy(precision="fp32"), sc) as s:
+            s.step(300)
+            xw, _, _ = s.state()
+        err_walk = np.max(np.abs(xw - ref.x))
+        disp = np.max(np.linalg.norm(ref.x - sc.x, axis=1))
+        assert err <= 2.0 * err_walk + 1e-6 * disp, (err, err_walk)
     assert d["pair_contacts"] + d["wall_contacts"] > 0
 
 
