@@ -505,7 +505,8 @@ def run_ours(args):
         xs, vs, ws = dem.dem_get_state(h, N)
         every = None
         if p.resort_interval != 1:
-            hk = dem.dem_create(dem.config_from_params(sc.params), dev.index, stream.cuda_stream)
+            hk = dem.dem_create(dem.config_from_params(sc.params, block_size=block, max_contacts=args.max_contacts),
+                                dev.index, stream.cuda_stream)
             try:
                 dem.dem_set_walls(hk, sc.params.walls)
                 dem.dem_set_particles(hk, xs, vs, ws, sc.r)
@@ -527,7 +528,8 @@ def run_ours(args):
         # ---------------- practical / simple on the same settled bed
         simple = None
         if args.simple_steps > 0:
-            hs = dem.dem_create(dem.config_from_params(p.copy(model="simple")), dev.index, stream.cuda_stream)
+            hs = dem.dem_create(dem.config_from_params(p.copy(model="simple"), block_size=block,
+                                                       max_contacts=args.max_contacts), dev.index, stream.cuda_stream)
             try:
                 dem.dem_set_walls(hs, p.walls)
                 dem.dem_set_particles(hs, xs, vs, ws, sc.r)
