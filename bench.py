@@ -131,7 +131,7 @@ def settle_bed(dem, sc, dev_index, stream, steps, relax):
         dem.dem_destroy(hs)
 
 
-def run_batch_bench(args, dem, dev_index, stream):
+def run_batch_bench(args, dem, dev_index, stream, block=0):
     """256 independent box-settling scenes (log-uniform 1,024-65,536 spheres, mu ~
     U[0.1, 0.6], e ~ U[0.5, 0.95]) advanced together in one batch, against the first
     scenes advanced one by one through their own handles."""
@@ -139,7 +139,8 @@ def run_batch_bench(args, dem, dev_index, stream):
     from paper_1301_1714_gb300 import scenes
     mix = scenes.batch_mix(seed=args.seed, count=args.batch_scenes, precision="fp32")
     total = sum(sc.n for sc in mix)
-    b = dem.dem_batch_create(precision="fp32", device=dev_index, cuda_stream=stream.cuda_stream)
+    b = dem.dem_batch_create(precision="fp32", max_contacts=args.max_contacts, block_size=block, device=dev_index,
+                             cuda_stream=stream.cuda_stream)
     try:
         for sc in mix:
             dem.dem_batch_add(b, sc.params, sc.x, sc.v, sc.w, sc.r, args.batch_steps + 3)
@@ -154,7 +155,8 @@ def run_batch_bench(args, dem, dev_index, stream):
         dem.dem_batch_destroy(b)
     seq_n, seq_t = 0, 0.0
     for sc in mix[:args.batch_seq_scenes]:
-        h = dem.dem_create(dem.config_from_params(sc.params), dev_index, stream.cuda_stream)
+        h = dem.dem_create(dem.config_from_params(sc.params, block_size=block, max_contacts=args.max_contacts),
+                           dev_index, stream.cuda_stream)
         try:
             dem.dem_set_walls(h, sc.params.walls)
             dem.dem_set_particles(h, sc.x, sc.v, sc.w, sc.r)
@@ -582,7 +584,7 @@ def run_ours(args):
                    "note": "one upload of the state, K steps, one download of the state (pinned host buffers), "
                            "through dem_set_particles / dem_step / dem_get_state"}
 
-        batch = run_batch_bench(args, dem, dev.index, stream) if args.batch_scenes > 0 else None
+        batch = run_batch_bench(args, dem, dev.index, stream, block) if args.batch_scenes > 0 else None
         serving = run_serve_bench(args, dem, dev.index, stream) if args.serve_requests > 0 else None
         hopper = (run_hopper_bench(args, dem, dev.index, stream, block)
                   if args.hopper_steps > 0 and rank == 0 and world == 1 else None)
