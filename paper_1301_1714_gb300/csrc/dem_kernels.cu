@@ -19,11 +19,11 @@
 #include "dem_domain.h"
 
 // Minimum resident 256-thread blocks per SM requested for the force kernel, which caps
-// its registers at 65536 / (256 * value): 80 registers in walk mode, 64 in list mode
-// (measured on GB300: the list-mode pass is 11% faster at 64 than at 80, the walk-mode
-// pass slightly slower).
+// its registers at 65536 / (256 * value): 64 registers in both modes (measured on
+// GB300: the list-mode pass is 11% faster at 64 than at 80; the walk-mode pass, once it
+// stopped prefetching its candidates' payload, 10% faster; 48 spills and is 19% slower).
 #ifndef DEM_FORCE_MIN_BLOCKS
-#define DEM_FORCE_MIN_BLOCKS 3
+#define DEM_FORCE_MIN_BLOCKS 4
 #endif
 #ifndef DEM_FORCE_MIN_BLOCKS_LIST
 #define DEM_FORCE_MIN_BLOCKS_LIST 4
