@@ -507,7 +507,12 @@ def run_ours(args):
         xs, vs, ws = dem.dem_get_state(h, N)
         every = None
         if p.resort_interval != 1:
-            hk = dem.dem_create(dem.config_from_params(sc.params, block_size=block, max_contacts=args.max_contacts),
+            wblock = block
+            if tuned:   # the walk's own best block size among the tuned candidates
+                walk = [row for row in tuned["table"] if row[1] == 1]
+                if walk:
+                    wblock = min(walk, key=lambda row: row[3])[0]
+            hk = dem.dem_create(dem.config_from_params(sc.params, block_size=wblock, max_contacts=args.max_contacts),
                                 dev.index, stream.cuda_stream)
             try:
                 dem.dem_set_walls(hk, sc.params.walls)
