@@ -60,6 +60,15 @@ def test_config_validation_on_host(lib):
     bad.block_size = 100
     assert dem.lib().dem_create(ctypes.byref(bad), 0, None, ctypes.byref(h)) == 1
     assert dem.lib().dem_create(None, 0, None, ctypes.byref(h)) == 1
+    for field, value in (("terms", 16), ("mu_roll", -1.0), ("alpha_t", float("inf")), ("k_coh", float("nan")),
+                         ("max_contacts", 65), ("resort_interval", 0)):
+        bad = dem.config_from_params(sc.params)
+        setattr(bad, field, value)
+        if field == "resort_interval":
+            bad.skin = 0.0                      # skin-driven sorting needs a skin
+        assert dem.lib().dem_create(ctypes.byref(bad), 0, None, ctypes.byref(h)) == 1, field
+    bad = dem.config_from_params(sc.params.copy(model="simple", terms=1))
+    assert dem.lib().dem_create(ctypes.byref(bad), 0, None, ctypes.byref(h)) == 1
     assert h.value is None
 
 
