@@ -43,7 +43,11 @@ def tune(params, x, v, w, r, candidates: Sequence[Tuple[int, int, float]] = DEFA
     for block, resort, sk in candidates:
         c = Choice(block, resort, sk, 0.0, 0.0, 0.0)
         p = apply(params, rmax, c)
-        h = dem.dem_create(dem.config_from_params(p, block_size=block, max_contacts=max_contacts), device, cuda_stream)
+        try:
+            h = dem.dem_create(dem.config_from_params(p, block_size=block, max_contacts=max_contacts), device,
+                               cuda_stream)
+        except dem.DemError:
+            continue                      # a candidate this configuration does not allow
         try:
             dem.dem_set_walls(h, p.walls)
             dem.dem_set_particles(h, x, v, w, r)
@@ -51,11 +55,17 @@ def tune(params, x, v, w, r, candidates: Sequence[Tuple[int, int, float]] = DEFA
             dem.dem_set_timing(h, True)
             dem.dem_step(h, steps)
             ph = dem.dem_get_phase_times(h)
+        except dem.DemError as e:
+            if e.status != dem.DEM_ERR_CAPACITY:
+                raise
+            continue                      # too many contacts for the capacity: not a candidate
         finally:
             dem.dem_destroy(h)
         c.force_ms = ph[0] / max(ph[2], 1)
         c.sort_ms = ph[1] / max(ph[3], 1)
         c.ms_per_step = c.force_ms + c.sort_ms
         table.append(c)
+    if not table:
+        raise RuntimeError("no autotune candidate ran (contact capacity too small for every one)")
     best = min(table, key=lambda t: t.ms_per_step)
     return best, table

@@ -17,6 +17,8 @@ from . import _build
 DEM_OK = 0
 DEM_ERR = {1: "DEM_ERR_INVALID_ARG", 2: "DEM_ERR_OOM", 3: "DEM_ERR_CUDA", 4: "DEM_ERR_CAPACITY",
            5: "DEM_ERR_TIMEOUT", 6: "DEM_ERR_NONFINITE", 7: "DEM_ERR_STATE"}
+(DEM_ERR_INVALID_ARG, DEM_ERR_OOM, DEM_ERR_CUDA, DEM_ERR_CAPACITY, DEM_ERR_TIMEOUT, DEM_ERR_NONFINITE,
+ DEM_ERR_STATE) = range(1, 8)
 DEM_PRACTICAL, DEM_SIMPLE = 0, 1
 DEM_LINEAR, DEM_HERTZ = 0, 1
 DEM_FP64, DEM_FP32 = 0, 1
