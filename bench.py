@@ -76,6 +76,10 @@ def parse():
     ap.add_argument("--serve-nmax", type=int, default=131072)
     ap.add_argument("--serve-steps", type=str, default="500,2000", help="step budget range of the requests")
     ap.add_argument("--serve-hbm-gb", type=float, default=16.0)
+    ap.add_argument("--slabs", type=str, default="2,4",
+                    help="slab counts of the decomposed runs (sub-domains with halo exchange, sort every step; "
+                         "'' = skip)")
+    ap.add_argument("--slab-steps", type=int, default=100, help="timed steps of each decomposed run")
     ap.add_argument("--hopper-steps", type=int, default=2000,
                     help="timed steps of the hopper comparison (the paper's own benchmark shape; 0 = skip)")
     ap.add_argument("--hopper-settle", type=int, default=3000, help="fill steps (closed bottom) before the slit opens")
@@ -234,6 +238,53 @@ def run_hopper_bench(args, dem, dev_index, stream, block=0):
                                    "simple_gpu_cuda_c2050": 2.2359e7, "practical_cpu_x5670_1core": 4.74e5,
                                    "note": "another machine and an unstated geometry: context, not a target"}
     return out
+
+
+def run_slab_bench(args, dem, dev_index, stream, sc, xs, vs, ws, every):
+    """The settled bed divided into slabs along its longest axis (sub-domains with a ghost
+    layer, exchange after every force pass, sort every step), against one undivided
+    handle in the same mode (`every`). The exchange reads its counts back every step."""
+    import torch
+    counts = [int(k) for k in args.slabs.split(",") if k.strip()]
+    if not counts or args.slab_steps <= 0:
+        return None
+    N = len(sc.r)
+    p = sc.params.copy(resort_interval=1, skin=0.0)
+    rows = {}
+    for S in counts:
+        sl = dem.dem_slabs_create(dem.config_from_params(p, block_size=256, max_contacts=args.max_contacts), S, -1,
+                                  dev_index, stream.cuda_stream)
+        try:
+            dem.dem_slabs_set_walls(sl, p.walls)
+            dem.dem_slabs_set_particles(sl, xs, vs, ws, sc.r)
+            dem.dem_slabs_step(sl, 3)
+            torch.cuda.synchronize(dev_index)
+            L0 = dem.dem_slabs_launch_count(sl)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            t0 = time.perf_counter()
+            nvtx_push(f"slabs{S}")
+            e0.record(stream)
+            dem.dem_slabs_step(sl, args.slab_steps)
+            e1.record(stream)
+            torch.cuda.synchronize(dev_index)
+            nvtx_pop()
+            wall = time.perf_counter() - t0
+            ms = e0.elapsed_time(e1) / args.slab_steps
+            info = dem.dem_slabs_info(sl, S)
+            rows[str(S)] = {"value": round(N / (ms / 1e3), 1), "ms_per_step": round(ms, 4),
+                            "host_ms_per_step": round(wall * 1e3 / args.slab_steps, 4),
+                            "ghost_fraction": round(float(info["ghosts"].sum()) / N, 4),
+                            "owned_min_max": [int(info["owned"].min()), int(info["owned"].max())],
+                            "migrated_per_step": round(info["migrated"] / max(info["steps"], 1), 1),
+                            "launches_per_step": round((dem.dem_slabs_launch_count(sl) - L0) / args.slab_steps, 1),
+                            "over_undivided": (round((N / (ms / 1e3)) / every["value"], 3) if every else None)}
+        finally:
+            dem.dem_slabs_destroy(sl)
+    return {"unit": UNIT, "steps": args.slab_steps, "block": 256, "rows": rows,
+            "note": "one scene as S sub-domains on one GPU: force pass per slab (ghosts included), one exchange "
+                    "launch (migration with springs, fresh ghost copies), a host read of the slab counts, a cell "
+                    "sort per slab; owned particles are bit-exact against the undivided run"}
 
 
 def run_serve_bench(args, dem, dev_index, stream):
@@ -532,6 +583,9 @@ def run_ours(args):
             finally:
                 dem.dem_destroy(hk)
 
+        # ---------------- the same bed as slabs (sub-domains with halo exchange), sort every step
+        slabs = run_slab_bench(args, dem, dev.index, stream, sc, xs, vs, ws, every) if rank == 0 else None
+
         # ---------------- practical / simple on the same settled bed
         simple = None
         if args.simple_steps > 0:
@@ -605,6 +659,7 @@ def run_ours(args):
                "roofline": roof, "gpu_launches": int(launches), "clocks": clocks, "graph_replay": graph,
                "simple": simple, "e2e": e2e,
                "batch": batch, "serving": serving, "hopper": hopper, "autotune": tuned, "sort_every_step": every,
+               "slabs": slabs,
                "diagnostics": dict({k: diag[k] for k in ("pair_contacts", "wall_contacts", "max_overlap", "ke_trans")},
                                    max_contacts_seen=max_seen, max_contacts=cfg.max_contacts or 32)}
     finally:

@@ -298,6 +298,76 @@ void dem_batch_destroy(dem_batch* b);
 dem_status dem_sort_cells_static(int64_t n, const double* x, const double* origin, double cell, const int64_t* dims,
                                  uint32_t* cell_of, uint32_t* order, uint32_t* cell_start, void* cuda_stream);
 
+/* ------------------------------------------------------------------------------------
+ * Slab decomposition with halo exchange (sub-domains of one scene on one device).
+ *
+ * The scene is cut along one axis into nslabs slabs (sub-domains) at the boundaries
+ * bounds[1..nslabs-1] (bounds[0] = -inf, bounds[nslabs] = +inf). Each slab has its own
+ * particle buffers and cell table on the scene's global grid (Sec. 4.1). A particle is
+ * OWNED by the slab whose range [bounds[s], bounds[s+1]) holds its coordinate along the
+ * axis and is a GHOST of every other slab within one cell edge h of its range. Because
+ * a contact needs a distance below r_i + r_j <= 2 r_max < h, every contact partner of an
+ * owned particle is present in its slab, and the 27-cell walk of Eq. 12 meets them in the
+ * (cell, id) order of Eq. 11 of the undivided scene: owned particles get the same bits
+ * as a dem_handle with the same configuration.
+ * A step: the force pass of every slab (steps 5-8 and 1 of Sec. 4.2; the ghosts' own
+ * results are discarded), one exchange launch that sends every owned particle with its
+ * tangential springs (Eq. 7) to the slab that owns its new position (migration) and a
+ * ghost copy to each slab whose ghost layer holds it (halo exchange), then the cell sort
+ * (steps 2-4) of every slab. In a run over several devices the exchange is the step
+ * that would cross devices; here the slabs share one device and one stream.
+ * Only the walk mode runs this way (dem_config.resort_interval must be 1). Each slab's
+ * buffers hold up to n particles, so no exchange can overflow. The exchange reads its
+ * counts back to the host every step (the slabs' particle counts set the launches of
+ * the sort), so dem_slabs_step synchronises the stream once per step.
+ * ------------------------------------------------------------------------------------ */
+typedef struct dem_slabs dem_slabs;
+
+#define DEM_MAX_SLABS 8
+
+/* Boundaries that split n coordinates z (host) into nslabs slabs of nearly equal counts:
+ * bounds (nslabs + 1 doubles, out) = -inf, the (k n / nslabs)-th smallest z for
+ * k = 1 .. nslabs - 1, +inf. Host only (no GPU needed). DEM_ERR_INVALID_ARG for nslabs
+ * outside [1, DEM_MAX_SLABS], n < 0, a NULL pointer or a non-finite z. */
+dem_status dem_slab_bounds(int64_t n, const double* z, int nslabs, double* bounds);
+
+/* Slabs of one scene: cfg as for dem_create (resort_interval must be 1); axis 0, 1 or 2,
+ * or -1 for the axis along which the configured domain is longest (the last of equal
+ * ones). The slabs share the device and the stream. */
+dem_status dem_slabs_create(const dem_config* cfg, int nslabs, int axis, int device, void* cuda_stream,
+                            dem_slabs** out);
+
+/* Walls of the scene, given to every slab (as dem_set_walls). */
+dem_status dem_slabs_set_walls(dem_slabs* s, int nwalls, const dem_wall* walls);
+
+/* Particles of the scene (as dem_set_particles; particle k has id k): the boundaries
+ * are chosen by dem_slab_bounds over the coordinates along the axis, every particle goes
+ * to its owning slab and to the ghost layers that hold it, and every slab sorts. */
+dem_status dem_slabs_set_particles(dem_slabs* s, int64_t n, const double* x, const double* v, const double* w,
+                                   const float* r, int where);
+
+/* nsteps steps of the whole scene (force passes, exchange, sorts); returns once they are
+ * done. DEM_ERR_CAPACITY / DEM_ERR_NONFINITE as dem_step, from any slab. */
+dem_status dem_slabs_step(dem_slabs* s, int64_t nsteps);
+
+/* State of every particle, from its owning slab, at 3 * id (as dem_get_state). */
+dem_status dem_slabs_get_state(dem_slabs* s, double* x, double* v, double* w, int where);
+
+/* After the last exchange (or the first distribution): owned[k] and ghosts[k] particles
+ * of slab k (nslabs entries each), the boundaries (nslabs + 1), the owned particles that
+ * changed slab summed over all steps, and the steps done. Any pointer may be NULL. */
+dem_status dem_slabs_info(const dem_slabs* s, int64_t* owned, int64_t* ghosts, double* bounds, int64_t* migrated,
+                          int64_t* steps);
+
+/* Kernel launches enqueued so far by all slabs and the exchange. */
+int64_t dem_slabs_launch_count(const dem_slabs* s);
+
+/* Last error message ("" if none). */
+const char* dem_slabs_last_error(const dem_slabs* s);
+
+/* Frees the slabs and their device memory. NULL is allowed. */
+void dem_slabs_destroy(dem_slabs* s);
+
 /* Bytes of device memory held by the handle. */
 int64_t dem_device_bytes(const dem_handle* h);
 

@@ -9,11 +9,13 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
 #include "dem.h"
 #include "dem_domain.h"
+#include "dem_halo.h"
 
 using namespace demgb;
 
@@ -382,6 +384,27 @@ dem_status rotate_counters(dem_handle* h) {
     return DEM_OK;
 }
 
+// Grid of Sec. 4.1 over the configured domain: cell edge >= one diameter of the largest
+// sphere (+ a 2^-10 margin, + skin), or the configured cell size.
+dem_status set_grid(dem_handle* h, bool any, double rmax, int64_t& nc) {
+    const dem_config& c = h->cfg;
+    const double hmin = 2.0 * rmax * (1.0 + std::ldexp(1.0, -10)) + c.skin;
+    double hc = c.cell_size > 0.0 ? c.cell_size : hmin;
+    if (any && hc < hmin * (1.0 - 1e-12))
+        return fail(h, DEM_ERR_INVALID_ARG, "cell_size is smaller than 2 r_max (1 + 2^-10) + skin");
+    if (!any && !(hc > 0.0)) hc = 1.0;
+    nc = 1;
+    for (int a = 0; a < 3; ++a) {
+        h->origin[a] = c.domain_lo[a];
+        h->dims[a] = std::max<int64_t>(1, (int64_t)std::ceil((c.domain_hi[a] - c.domain_lo[a]) / hc));
+        nc *= h->dims[a];
+        if (nc > (int64_t)0x7FFFFFFF) return fail(h, DEM_ERR_INVALID_ARG, "grid has more than 2^31 cells");
+    }
+    h->h = hc;
+    h->rmax = rmax;
+    return DEM_OK;
+}
+
 // Upload (or take from the device) particle arrays, build the grid and do the first sort.
 dem_status load_particles(dem_handle* h, int64_t n64, const double* x, const double* v, const double* w,
                           const float* r, int where) {
@@ -408,25 +431,13 @@ dem_status load_particles(dem_handle* h, int64_t n64, const double* x, const dou
         for (uint32_t k = 0; k < n; ++k)
             if (!finite3(x + 3 * (size_t)k) || !finite3(v + 3 * (size_t)k) || !finite3(w + 3 * (size_t)k))
                 return fail(h, DEM_ERR_INVALID_ARG, "non-finite position, velocity or spin in the input");
-    // grid (Sec. 4.1): edge >= one diameter of the largest sphere (+ margin, + skin)
     const dem_config& c = h->cfg;
-    const double hmin = 2.0 * rmax * (1.0 + std::ldexp(1.0, -10)) + c.skin;
-    double hc = c.cell_size > 0.0 ? c.cell_size : hmin;
-    if (n > 0 && hc < hmin * (1.0 - 1e-12))
-        return fail(h, DEM_ERR_INVALID_ARG, "cell_size is smaller than 2 r_max (1 + 2^-10) + skin");
-    if (n == 0 && !(hc > 0.0)) hc = 1.0;
     int64_t nc = 1;
-    for (int a = 0; a < 3; ++a) {
-        h->origin[a] = c.domain_lo[a];
-        h->dims[a] = std::max<int64_t>(1, (int64_t)std::ceil((c.domain_hi[a] - c.domain_lo[a]) / hc));
-        nc *= h->dims[a];
-        if (nc > (int64_t)0x7FFFFFFF) return fail(h, DEM_ERR_INVALID_ARG, "grid has more than 2^31 cells");
-    }
-    h->h = hc;
-    h->rmax = rmax;
+    dem_status s = set_grid(h, n > 0, rmax, nc);
+    if (s != DEM_OK) return s;
     d.n = n;
     d.ncells = (uint32_t)nc;
-    dem_status s = ensure_buffers(h, n, (uint32_t)nc);
+    s = ensure_buffers(h, n, (uint32_t)nc);
     if (s != DEM_OK) return s;
     // scene table (one scene)
     d.nscenes = 1;
@@ -1643,6 +1654,491 @@ void dem_batch_destroy(dem_batch* b) {
     if (b->d_map) cudaFree(b->d_map);
     cudaGetLastError();
     delete b;
+}
+
+}  // extern "C"
+
+// =========================================================================== slabs
+// One scene divided along one axis into slabs (sub-domains), each a handle with its own
+// particle buffers and cell table on the scene's global grid and a ghost layer one cell
+// edge wide on each side (dem_halo.h). A step runs the force pass of every slab, one
+// exchange launch (migration of owned particles with their springs, fresh ghost copies),
+// the flip of every slab's current set (the exchange wrote into the set the force pass
+// read), and the cell sort of every slab's new layout.
+struct dem_slabs {
+    dem_config cfg{};
+    int device = 0;
+    int nslabs = 0;
+    int axis = 2;
+    cudaStream_t stream = nullptr;
+    std::vector<dem_handle*> sl;
+    std::vector<int> cur;              // host mirror of each slab's ctrl->cur
+    HaloGeom geom{};
+    uint8_t* owner[2] = {nullptr, nullptr};   // slab of every particle id, double-buffered
+    int own_cur = 0;                   // owner[own_cur] holds the current owners
+    uint32_t owner_cap = 0;
+    HaloCounters* hc = nullptr;        // device: counters of the exchange in flight
+    HaloCounters* hc_host = nullptr;   // pinned: counters of the last exchange
+    std::vector<uint8_t> io_table;     // SlabIO table of the exchange (host; passed by value)
+    void* io_host = nullptr;
+    double* stage = nullptr;           // host input / output staging: x, v, w (3n doubles each)
+    float* stage_r = nullptr;
+    uint32_t stage_cap = 0;
+    uint32_t n = 0;
+    bool has_particles = false;
+    bool broken = false;
+    int64_t steps = 0;
+    int64_t migrated = 0;
+    int64_t launches = 0;              // exchange, flip and export launches
+    std::string err;
+};
+
+namespace {
+
+dem_status sfail(dem_slabs* S, dem_status st, const std::string& m) {
+    if (S) S->err = m;
+    return st;
+}
+
+dem_status scuda(dem_slabs* S, cudaError_t e, const char* what) {
+    S->broken = true;
+    S->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return DEM_ERR_CUDA;
+}
+
+#define SCK(S, expr)                                                       \
+    do {                                                                   \
+        cudaError_t e__ = (expr);                                          \
+        if (e__ != cudaSuccess) return scuda((S), e__, #expr);             \
+    } while (0)
+
+// A slab's error (from its handle) becomes the slabs' error.
+dem_status from_slab(dem_slabs* S, int k, dem_status st) {
+    if (st == DEM_OK) return st;
+    if (S->sl[k]->broken) S->broken = true;
+    S->err = "slab " + std::to_string(k) + ": " + S->sl[k]->err;
+    return st;
+}
+
+// Buffers of an empty slab for up to cap particles on the scene's grid, a scene table,
+// cleared status and spring counts, and a step control that sorts next.
+dem_status slab_prepare(dem_handle* h, uint32_t cap, double rmax) {
+    Domain& d = h->d;
+    h->graph.reset();
+    int64_t nc = 1;
+    dem_status s = set_grid(h, cap > 0, rmax, nc);
+    if (s != DEM_OK) return s;
+    d.n = 0;
+    d.ncells = (uint32_t)nc;
+    s = ensure_buffers(h, cap, (uint32_t)nc);
+    if (s != DEM_OK) return s;
+    d.nscenes = 1;
+    d.h_scenes.assign(1, SceneDev{});
+    fill_scene(h, d.h_scenes[0], 0, cap, 0);
+    if (!d.d_scenes) {
+        if (cudaMalloc(&d.d_scenes, sizeof(SceneDev)) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, DEM_ERR_OOM, "cudaMalloc(scene table) failed");
+        }
+        d.scenes_cap = 1;
+    }
+    CK(h, cudaMemcpyAsync(d.d_scenes, d.h_scenes.data(), sizeof(SceneDev), cudaMemcpyHostToDevice, d.stream));
+    CK(h, cudaMemsetAsync(d.st, 0, sizeof(StatusDev), d.stream));
+    CK(h, cudaMemsetAsync(d.cnt, 0, ((size_t)d.ncells + 1) * 4, d.stream));
+    *d.ctrl_host = CtrlDev{};
+    d.ctrl_host->rebuild = 1;
+    CK(h, cudaMemcpyAsync(d.ctrl, d.ctrl_host, sizeof(CtrlDev), cudaMemcpyHostToDevice, d.stream));
+    d.h_cur = 0;
+    CK(h, cudaMemsetAsync(d.hcnt[0], 0, (size_t)d.cap * 4, d.stream));
+    CK(h, cudaMemsetAsync(d.hcnt[1], 0, (size_t)d.cap * 4, d.stream));
+    h->has_particles = true;
+    h->eval_valid = false;
+    h->steps = 0;
+    return DEM_OK;
+}
+
+// Exchange table: sources are the sets and springs the force pass just wrote; each
+// destination is the set the force pass read (import: the set the first sort gathers
+// from) and the spring buffer not holding the sources.
+template <class St, class T>
+void fill_io(dem_slabs* S, bool import, uint32_t& ntotal) {
+    auto* io = (SlabIO<St, T>*)S->io_host;
+    uint32_t p0 = 0;
+    for (int k = 0; k < S->nslabs; ++k) {
+        Domain& d = S->sl[k]->d;
+        SlabIO<St, T> e{};
+        const int c = S->cur[k];
+        St sets[2];
+        if constexpr (sizeof(T) == 8) { sets[0] = d.S64[0]; sets[1] = d.S64[1]; }
+        else { sets[0] = d.S32[0]; sets[1] = d.S32[1]; }
+        const int hs = d.h_cur;            // springs written by the force pass
+        const int hd = import ? d.h_cur : 1 - d.h_cur;
+        e.src = sets[1 - c];
+        e.dst = import ? sets[1 - c] : sets[c];
+        e.hcnt_src = d.hcnt[hs];
+        e.hpid_src = d.hpid[hs];
+        e.hd_src = (const T*)d.hd[hs];
+        e.hcnt_dst = d.hcnt[hd];
+        e.hpid_dst = d.hpid[hd];
+        e.hd_dst = (T*)d.hd[hd];
+        e.n = import ? 0u : d.n;
+        e.p0 = p0;
+        e.cap = d.cap;
+        p0 += e.n;
+        io[k] = e;
+    }
+    ntotal = p0;
+}
+
+// The exchange table (passed to the exchange kernel by value) and cleared counters.
+dem_status prepare_exchange(dem_slabs* S, bool import, uint32_t& ntotal) {
+    if (S->cfg.precision == 0) fill_io<StateF64, double>(S, import, ntotal);
+    else fill_io<StateF32, float>(S, import, ntotal);
+    SCK(S, cudaMemsetAsync(S->hc, 0, sizeof(HaloCounters), S->stream));
+    return DEM_OK;
+}
+
+// After an exchange: its counters on the host, the new particle count of every slab.
+dem_status take_counts(dem_slabs* S) {
+    SCK(S, cudaMemcpyAsync(S->hc_host, S->hc, sizeof(HaloCounters), cudaMemcpyDeviceToHost, S->stream));
+    SCK(S, cudaStreamSynchronize(S->stream));
+    if (S->hc_host->overflow)
+        return sfail(S, DEM_ERR_CAPACITY, "slab exchange overflowed a slab's capacity");
+    for (int k = 0; k < S->nslabs; ++k) S->sl[k]->d.n = S->hc_host->fill[k];
+    return DEM_OK;
+}
+
+// Cell sort of every slab's new layout (the set that is "next" for its step control).
+dem_status sort_slabs(dem_slabs* S) {
+    for (int k = 0; k < S->nslabs; ++k) {
+        dem_handle* h = S->sl[k];
+        Domain& d = h->d;
+        // cell counts from scratch (the force pass counted the layout before the exchange)
+        cudaError_t e = cudaMemsetAsync(d.cnt, 0, ((size_t)d.ncells + 1) * 4, d.stream);
+        if (e == cudaSuccess && d.n > 0) e = run_hash(d);
+        if (e == cudaSuccess && d.n > 0) e = run_rebuild(d);
+        if (e == cudaSuccess) e = run_end_step(d);
+        if (e != cudaSuccess) return from_slab(S, k, cuda_fail(h, e, "slab sort"));
+    }
+    return DEM_OK;
+}
+
+dem_status slabs_one_step(dem_slabs* S) {
+    for (int k = 0; k < S->nslabs; ++k) {
+        Domain& d = S->sl[k]->d;
+        if (d.n > 0) {
+            cudaError_t e = run_force(d, false, nullptr, nullptr);
+            if (e != cudaSuccess) return from_slab(S, k, cuda_fail(S->sl[k], e, "slab force pass"));
+        }
+        d.h_cur = 1 - d.h_cur;   // springs just written
+    }
+    uint32_t ntotal = 0;
+    dem_status st = prepare_exchange(S, false, ntotal);
+    if (st != DEM_OK) return st;
+    SCK(S, run_halo_route(S->cfg.precision, S->io_host, S->geom, ntotal, (uint32_t)S->sl[0]->d.maxc,
+                          S->owner[S->own_cur], S->owner[1 - S->own_cur], S->hc, S->sl[0]->d.sort_blocks, S->stream));
+    CtrlTable t{};
+    t.n = S->nslabs;
+    for (int k = 0; k < S->nslabs; ++k) t.c[k] = S->sl[k]->d.ctrl;
+    SCK(S, run_halo_flip(t, S->stream));
+    S->launches += ntotal ? 2 : 1;
+    st = take_counts(S);
+    if (st != DEM_OK) return st;
+    S->own_cur ^= 1;
+    S->migrated += S->hc_host->migrated;
+    for (int k = 0; k < S->nslabs; ++k) {
+        S->cur[k] ^= 1;
+        S->sl[k]->d.h_cur = 1 - S->sl[k]->d.h_cur;   // the exchanged springs
+    }
+    return sort_slabs(S);
+}
+
+}  // namespace
+
+extern "C" {
+
+dem_status dem_slab_bounds(int64_t n, const double* z, int nslabs, double* bounds) {
+    if (nslabs < 1 || nslabs > DEM_MAX_SLABS || n < 0 || !bounds || (n > 0 && !z)) return DEM_ERR_INVALID_ARG;
+    std::vector<double> v(z, z + n);
+    for (double a : v)
+        if (!std::isfinite(a)) return DEM_ERR_INVALID_ARG;
+    const double inf = std::numeric_limits<double>::infinity();
+    bounds[0] = -inf;
+    bounds[nslabs] = inf;
+    size_t lo = 0;
+    for (int k = 1; k < nslabs; ++k) {
+        const size_t idx = (size_t)((n * (int64_t)k) / nslabs);
+        if (n == 0) {
+            bounds[k] = inf;
+            continue;
+        }
+        if (idx >= lo) std::nth_element(v.begin() + lo, v.begin() + idx, v.end());
+        bounds[k] = v[idx];
+        lo = idx + 1;
+    }
+    return DEM_OK;
+}
+
+dem_status dem_slabs_create(const dem_config* cfg, int nslabs, int axis, int device, void* cuda_stream,
+                            dem_slabs** out) {
+    if (!out) return DEM_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!cfg || nslabs < 1 || nslabs > DEM_MAX_SLABS || axis < -1 || axis > 2) return DEM_ERR_INVALID_ARG;
+    if (cfg->resort_interval != 1) return DEM_ERR_INVALID_ARG;   // the walk mode only
+    std::string why;
+    dem_status st = validate_config(cfg, why);
+    if (st != DEM_OK) return st;
+    if (axis < 0) {
+        axis = 0;
+        for (int a = 1; a < 3; ++a)
+            if (cfg->domain_hi[a] - cfg->domain_lo[a] >= cfg->domain_hi[axis] - cfg->domain_lo[axis]) axis = a;
+    }
+    dem_slabs* S = new dem_slabs();
+    S->cfg = *cfg;
+    S->device = device;
+    S->nslabs = nslabs;
+    S->axis = axis;
+    S->stream = (cudaStream_t)cuda_stream;
+    for (int k = 0; k < nslabs; ++k) {
+        dem_handle* h = nullptr;
+        st = dem_create(cfg, device, cuda_stream, &h);
+        if (st != DEM_OK) {
+            dem_slabs_destroy(S);
+            return st;
+        }
+        S->sl.push_back(h);
+    }
+    S->cur.assign(nslabs, 0);
+    DeviceGuard g(device);
+    const size_t iob = std::max(sizeof(SlabIO<StateF64, double>), sizeof(SlabIO<StateF32, float>)) * DEM_MAX_SLABS;
+    S->io_table.assign(iob, 0);
+    S->io_host = S->io_table.data();
+    if (cudaMalloc(&S->hc, sizeof(HaloCounters)) != cudaSuccess ||
+        cudaMallocHost(&S->hc_host, sizeof(HaloCounters)) != cudaSuccess) {
+        cudaGetLastError();
+        dem_slabs_destroy(S);
+        return DEM_ERR_OOM;
+    }
+    std::memset(S->hc_host, 0, sizeof(HaloCounters));
+    *out = S;
+    return DEM_OK;
+}
+
+dem_status dem_slabs_set_walls(dem_slabs* S, int nwalls, const dem_wall* walls) {
+    if (!S) return DEM_ERR_INVALID_ARG;
+    if (S->broken) return sfail(S, DEM_ERR_STATE, "slabs are unusable after a CUDA error");
+    for (int k = 0; k < S->nslabs; ++k) {
+        dem_status st = dem_set_walls(S->sl[k], nwalls, walls);
+        if (st != DEM_OK) return from_slab(S, k, st);
+    }
+    return DEM_OK;
+}
+
+dem_status dem_slabs_set_particles(dem_slabs* S, int64_t n64, const double* x, const double* v, const double* w,
+                                   const float* r, int where) {
+    if (!S) return DEM_ERR_INVALID_ARG;
+    if (S->broken) return sfail(S, DEM_ERR_STATE, "slabs are unusable after a CUDA error");
+    if (n64 < 0 || n64 > (int64_t)0x7FFFFF00) return sfail(S, DEM_ERR_INVALID_ARG, "n out of range");
+    if (where != DEM_HOST && where != DEM_DEVICE) return sfail(S, DEM_ERR_INVALID_ARG, "where");
+    const uint32_t n = (uint32_t)n64;
+    if (n > 0 && (!x || !v || !w || !r)) return sfail(S, DEM_ERR_INVALID_ARG, "x, v, w and r are required");
+    DeviceGuard g(S->device);
+    S->has_particles = false;
+    // radii and the coordinates along the axis on the host (boundaries, grid)
+    std::vector<float> rh;
+    std::vector<double> xh;
+    const float* rr = r;
+    const double* xx = x;
+    if (n > 0 && where == DEM_DEVICE) {
+        rh.resize(n);
+        xh.resize(3 * (size_t)n);
+        SCK(S, cudaMemcpy(rh.data(), r, (size_t)n * 4, cudaMemcpyDeviceToHost));
+        SCK(S, cudaMemcpy(xh.data(), x, (size_t)n * 24, cudaMemcpyDeviceToHost));
+        rr = rh.data();
+        xx = xh.data();
+    }
+    double rmax = 0.0;
+    for (uint32_t k = 0; k < n; ++k) {
+        if (!(rr[k] > 0.f) || !std::isfinite(rr[k])) return sfail(S, DEM_ERR_INVALID_ARG, "radii must be finite and > 0");
+        rmax = std::max(rmax, (double)rr[k]);
+    }
+    if (where == DEM_HOST)
+        for (uint32_t k = 0; k < n; ++k)
+            if (!finite3(x + 3 * (size_t)k) || !finite3(v + 3 * (size_t)k) || !finite3(w + 3 * (size_t)k))
+                return sfail(S, DEM_ERR_INVALID_ARG, "non-finite position, velocity or spin in the input");
+    std::vector<double> za(n);
+    for (uint32_t k = 0; k < n; ++k) za[k] = xx[3 * (size_t)k + S->axis];
+    HaloGeom geom{};
+    geom.nslabs = S->nslabs;
+    geom.axis = S->axis;
+    if (dem_slab_bounds(n, za.data(), S->nslabs, geom.zb) != DEM_OK)
+        return sfail(S, DEM_ERR_INVALID_ARG, "non-finite coordinate along the slab axis");
+    for (int k = 0; k < S->nslabs; ++k) {
+        dem_status st = slab_prepare(S->sl[k], n, rmax);
+        if (st != DEM_OK) return from_slab(S, k, st);
+        S->cur[k] = 0;
+    }
+    geom.G = S->sl[0]->h;
+    S->geom = geom;
+    S->n = n;
+    if (n > S->owner_cap) {
+        for (auto& o : S->owner) {
+            if (o) cudaFree(o);
+            o = nullptr;
+        }
+        S->owner_cap = 0;
+        if (cudaMalloc(&S->owner[0], n) != cudaSuccess || cudaMalloc(&S->owner[1], n) != cudaSuccess) {
+            cudaGetLastError();
+            return sfail(S, DEM_ERR_OOM, "cudaMalloc(owner map) failed");
+        }
+        S->owner_cap = n;
+    }
+    S->own_cur = 0;
+    const double *xd = x, *vd = v, *wd = w;
+    const float* rd = r;
+    if (n > 0 && where == DEM_HOST) {
+        if (n > S->stage_cap) {
+            if (S->stage) cudaFree(S->stage);
+            if (S->stage_r) cudaFree(S->stage_r);
+            S->stage = nullptr;
+            S->stage_r = nullptr;
+            S->stage_cap = 0;
+            if (cudaMalloc(&S->stage, (size_t)n * 72) != cudaSuccess || cudaMalloc(&S->stage_r, (size_t)n * 4) != cudaSuccess) {
+                cudaGetLastError();
+                return sfail(S, DEM_ERR_OOM, "cudaMalloc(stage) failed");
+            }
+            S->stage_cap = n;
+        }
+        SCK(S, cudaMemcpyAsync(S->stage, x, (size_t)n * 24, cudaMemcpyHostToDevice, S->stream));
+        SCK(S, cudaMemcpyAsync(S->stage + 3 * (size_t)n, v, (size_t)n * 24, cudaMemcpyHostToDevice, S->stream));
+        SCK(S, cudaMemcpyAsync(S->stage + 6 * (size_t)n, w, (size_t)n * 24, cudaMemcpyHostToDevice, S->stream));
+        SCK(S, cudaMemcpyAsync(S->stage_r, r, (size_t)n * 4, cudaMemcpyHostToDevice, S->stream));
+        xd = S->stage; vd = S->stage + 3 * (size_t)n; wd = S->stage + 6 * (size_t)n; rd = S->stage_r;
+    }
+    uint32_t ntotal = 0;
+    dem_status st = prepare_exchange(S, true, ntotal);
+    if (st != DEM_OK) return st;
+    SCK(S, run_halo_import(S->cfg.precision, S->io_host, S->geom, n, xd, vd, wd, rd, S->owner[0], S->hc,
+                           S->sl[0]->d.sort_blocks, S->stream));
+    if (n > 0) S->launches += 1;
+    st = take_counts(S);
+    if (st != DEM_OK) return st;
+    st = sort_slabs(S);
+    if (st != DEM_OK) return st;
+    SCK(S, cudaStreamSynchronize(S->stream));
+    for (int k = 0; k < S->nslabs; ++k) {
+        st = sync_status(S->sl[k]);
+        if (st != DEM_OK) return from_slab(S, k, st);
+    }
+    S->has_particles = true;
+    S->steps = 0;
+    S->migrated = 0;
+    S->err.clear();
+    return DEM_OK;
+}
+
+dem_status dem_slabs_step(dem_slabs* S, int64_t nsteps) {
+    if (!S) return DEM_ERR_INVALID_ARG;
+    if (S->broken) return sfail(S, DEM_ERR_STATE, "slabs are unusable after a CUDA error");
+    if (!S->has_particles) return sfail(S, DEM_ERR_STATE, "dem_slabs_step before dem_slabs_set_particles");
+    if (nsteps < 0) return sfail(S, DEM_ERR_INVALID_ARG, "nsteps < 0");
+    DeviceGuard g(S->device);
+    for (int64_t i = 0; i < nsteps; ++i) {
+        dem_status st = slabs_one_step(S);
+        if (st != DEM_OK) return st;
+        ++S->steps;
+    }
+    SCK(S, cudaStreamSynchronize(S->stream));
+    for (int k = 0; k < S->nslabs; ++k) {
+        S->sl[k]->steps = S->steps;
+        dem_status st = sync_status(S->sl[k]);
+        if (st != DEM_OK) return from_slab(S, k, st);
+    }
+    return DEM_OK;
+}
+
+dem_status dem_slabs_get_state(dem_slabs* S, double* x, double* v, double* w, int where) {
+    if (!S) return DEM_ERR_INVALID_ARG;
+    if (S->broken) return sfail(S, DEM_ERR_STATE, "slabs are unusable after a CUDA error");
+    if (!S->has_particles) return sfail(S, DEM_ERR_STATE, "no particles");
+    if (where != DEM_HOST && where != DEM_DEVICE) return sfail(S, DEM_ERR_INVALID_ARG, "where");
+    DeviceGuard g(S->device);
+    const size_t n = S->n;
+    if (n == 0) return DEM_OK;
+    double *xo = x, *vo = v, *wo = w;
+    if (where == DEM_HOST) {
+        if (S->n > S->stage_cap) {
+            if (S->stage) cudaFree(S->stage);
+            if (S->stage_r) cudaFree(S->stage_r);
+            S->stage = nullptr;
+            S->stage_r = nullptr;
+            S->stage_cap = 0;
+            if (cudaMalloc(&S->stage, n * 72) != cudaSuccess || cudaMalloc(&S->stage_r, n * 4) != cudaSuccess) {
+                cudaGetLastError();
+                return sfail(S, DEM_ERR_OOM, "cudaMalloc(stage) failed");
+            }
+            S->stage_cap = S->n;
+        }
+        xo = x ? S->stage : nullptr;
+        vo = v ? S->stage + 3 * n : nullptr;
+        wo = w ? S->stage + 6 * n : nullptr;
+    }
+    for (int k = 0; k < S->nslabs; ++k) {
+        Domain& d = S->sl[k]->d;
+        if (d.n == 0) continue;
+        SCK(S, run_halo_export(d, k, S->owner[S->own_cur], xo, vo, wo));
+        S->launches += 1;
+    }
+    if (where == DEM_HOST) {
+        if (x) SCK(S, cudaMemcpyAsync(x, xo, n * 24, cudaMemcpyDeviceToHost, S->stream));
+        if (v) SCK(S, cudaMemcpyAsync(v, vo, n * 24, cudaMemcpyDeviceToHost, S->stream));
+        if (w) SCK(S, cudaMemcpyAsync(w, wo, n * 24, cudaMemcpyDeviceToHost, S->stream));
+    }
+    SCK(S, cudaStreamSynchronize(S->stream));
+    return DEM_OK;
+}
+
+dem_status dem_slabs_info(const dem_slabs* S, int64_t* owned, int64_t* ghosts, double* bounds, int64_t* migrated,
+                          int64_t* steps) {
+    if (!S) return DEM_ERR_INVALID_ARG;
+    for (int k = 0; k < S->nslabs; ++k) {
+        const int64_t f = S->has_particles ? S->hc_host->fill[k] : 0;
+        const int64_t o = S->has_particles ? S->hc_host->owned[k] : 0;
+        if (owned) owned[k] = o;
+        if (ghosts) ghosts[k] = f - o;
+    }
+    if (bounds)
+        for (int k = 0; k <= S->nslabs; ++k) bounds[k] = S->geom.zb[k];
+    if (migrated) *migrated = S->migrated;
+    if (steps) *steps = S->steps;
+    return DEM_OK;
+}
+
+int64_t dem_slabs_launch_count(const dem_slabs* S) {
+    if (!S) return 0;
+    int64_t L = S->launches;
+    for (dem_handle* h : S->sl) L += h->d.launches;
+    return L;
+}
+
+const char* dem_slabs_last_error(const dem_slabs* S) { return S ? S->err.c_str() : "null slabs"; }
+
+void dem_slabs_destroy(dem_slabs* S) {
+    if (!S) return;
+    {
+        DeviceGuard g(S->device);
+        if (S->stream) cudaStreamSynchronize(S->stream);
+        else cudaDeviceSynchronize();
+        for (auto& o : S->owner)
+            if (o) cudaFree(o);
+        if (S->hc) cudaFree(S->hc);
+        if (S->hc_host) cudaFreeHost(S->hc_host);
+        if (S->stage) cudaFree(S->stage);
+        if (S->stage_r) cudaFree(S->stage_r);
+        cudaGetLastError();
+    }
+    for (dem_handle* h : S->sl) dem_destroy(h);
+    delete S;
 }
 
 }  // extern "C"

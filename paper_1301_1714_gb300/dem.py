@@ -60,7 +60,11 @@ _EXPORTS = ["dem_create", "dem_set_particles", "dem_set_walls", "dem_step", "dem
             "dem_set_timing",
             "dem_get_phase_times", "dem_sort_cells_static", "dem_batch_create", "dem_batch_add", "dem_batch_run",
             "dem_batch_get_state", "dem_batch_remove", "dem_batch_info", "dem_batch_device_bytes",
-            "dem_batch_launch_count", "dem_batch_last_error", "dem_batch_destroy"]
+            "dem_batch_launch_count", "dem_batch_last_error", "dem_batch_destroy", "dem_slab_bounds",
+            "dem_slabs_create", "dem_slabs_set_walls", "dem_slabs_set_particles", "dem_slabs_step",
+            "dem_slabs_get_state", "dem_slabs_info", "dem_slabs_launch_count", "dem_slabs_last_error",
+            "dem_slabs_destroy"]
+DEM_MAX_SLABS = 8
 
 
 def lib_path() -> str:
@@ -105,6 +109,19 @@ def lib():
     L.dem_batch_last_error.restype = ctypes.c_char_p
     L.dem_batch_destroy.argtypes = [P]
     L.dem_batch_destroy.restype = None
+    L.dem_slab_bounds.argtypes = [I64, P, I32, P]
+    L.dem_slabs_create.argtypes = [ctypes.POINTER(dem_config), I32, I32, I32, P, ctypes.POINTER(P)]
+    L.dem_slabs_set_walls.argtypes = [P, I32, P]
+    L.dem_slabs_set_particles.argtypes = [P, I64, P, P, P, P, I32]
+    L.dem_slabs_step.argtypes = [P, I64]
+    L.dem_slabs_get_state.argtypes = [P, P, P, P, I32]
+    L.dem_slabs_info.argtypes = [P, P, P, P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
+    L.dem_slabs_launch_count.argtypes = [P]
+    L.dem_slabs_launch_count.restype = I64
+    L.dem_slabs_last_error.argtypes = [P]
+    L.dem_slabs_last_error.restype = ctypes.c_char_p
+    L.dem_slabs_destroy.argtypes = [P]
+    L.dem_slabs_destroy.restype = None
     L.dem_set_timing.argtypes = [P, I32]
     L.dem_get_phase_times.argtypes = [P, P]
     L.dem_device_bytes.argtypes = [P]
@@ -126,7 +143,9 @@ def lib():
                                                   "dem_set_timing", "dem_get_phase_times",
                                                   "dem_sort_cells_static", "dem_batch_create", "dem_batch_add",
                                                   "dem_batch_run", "dem_batch_get_state", "dem_batch_remove",
-                                                  "dem_batch_info"):
+                                                  "dem_batch_info", "dem_slab_bounds", "dem_slabs_create",
+                                                  "dem_slabs_set_walls", "dem_slabs_set_particles", "dem_slabs_step",
+                                                  "dem_slabs_get_state", "dem_slabs_info"):
             f.restype = ctypes.c_int
     _lib = L
     return L
@@ -488,3 +507,131 @@ def dem_batch_last_error(b):
 def dem_batch_destroy(b):
     if b:
         lib().dem_batch_destroy(b)
+
+
+# ------------------------------------------------------------------ slabs (sub-domains with halo exchange)
+def _scheck(sl, status):
+    if status != DEM_OK:
+        msg = lib().dem_slabs_last_error(sl).decode() if sl else ""
+        raise DemError(status, msg)
+
+
+def dem_slab_bounds(z, nslabs):
+    """Boundaries (nslabs + 1 doubles, -inf .. +inf) splitting the coordinates z into
+    nslabs slabs of nearly equal counts (host only)."""
+    z = np.ascontiguousarray(z, dtype=np.float64).ravel()
+    out = np.zeros(int(nslabs) + 1)
+    st = lib().dem_slab_bounds(len(z), _ptr(z), int(nslabs), _ptr(out))
+    if st != DEM_OK:
+        raise DemError(st, "dem_slab_bounds: nslabs outside [1, 8] or a non-finite coordinate")
+    return out
+
+
+def dem_slabs_create(config, nslabs, axis=-1, device=0, cuda_stream=None):
+    c = config if isinstance(config, dem_config) else config_from_params(config)
+    sl = ctypes.c_void_p()
+    st = lib().dem_slabs_create(ctypes.byref(c), int(nslabs), int(axis), device,
+                                ctypes.c_void_p(cuda_stream) if cuda_stream else None, ctypes.byref(sl))
+    if st != DEM_OK:
+        raise DemError(st, "dem_slabs_create rejected the configuration (resort_interval must be 1), "
+                           "the slab count, the axis or the device")
+    return sl
+
+
+def dem_slabs_set_walls(sl, walls):
+    arr = walls_array(walls)
+    _scheck(sl, lib().dem_slabs_set_walls(sl, len(walls), arr))
+
+
+def dem_slabs_set_particles(sl, x, v, w, r):
+    n = len(r)
+    if _is_device(r):
+        for t, dt in ((x, "torch.float64"), (v, "torch.float64"), (w, "torch.float64"), (r, "torch.float32")):
+            if not (_is_device(t) and str(t.dtype) == dt and t.is_contiguous()):
+                raise ValueError("device inputs must be contiguous CUDA tensors (x, v, w float64; r float32)")
+        _scheck(sl, lib().dem_slabs_set_particles(sl, n, _ptr(x), _ptr(v), _ptr(w), _ptr(r), DEM_DEVICE))
+        return
+    x = _host(x, np.float64, (n, 3)); v = _host(v, np.float64, (n, 3)); w = _host(w, np.float64, (n, 3))
+    r = _host(r, np.float32, (n,))
+    _scheck(sl, lib().dem_slabs_set_particles(sl, n, _ptr(x), _ptr(v), _ptr(w), _ptr(r), DEM_HOST))
+
+
+def dem_slabs_step(sl, nsteps=1):
+    _scheck(sl, lib().dem_slabs_step(sl, int(nsteps)))
+
+
+def dem_slabs_get_state(sl, n, x=None, v=None, w=None):
+    if _is_device(x) or _is_device(v) or _is_device(w):
+        _scheck(sl, lib().dem_slabs_get_state(sl, _ptr(x), _ptr(v), _ptr(w), DEM_DEVICE))
+        return x, v, w
+    x = np.zeros((n, 3)); v = np.zeros((n, 3)); w = np.zeros((n, 3))
+    _scheck(sl, lib().dem_slabs_get_state(sl, _ptr(x), _ptr(v), _ptr(w), DEM_HOST))
+    return x, v, w
+
+
+def dem_slabs_info(sl, nslabs):
+    """dict: owned and ghosts per slab, boundaries, migrations so far, steps done."""
+    owned = np.zeros(nslabs, np.int64); ghosts = np.zeros(nslabs, np.int64); bounds = np.zeros(nslabs + 1)
+    mig = ctypes.c_int64(0); steps = ctypes.c_int64(0)
+    _scheck(sl, lib().dem_slabs_info(sl, _ptr(owned), _ptr(ghosts), _ptr(bounds), ctypes.byref(mig),
+                                     ctypes.byref(steps)))
+    return {"owned": owned, "ghosts": ghosts, "bounds": bounds, "migrated": int(mig.value), "steps": int(steps.value)}
+
+
+def dem_slabs_launch_count(sl):
+    return int(lib().dem_slabs_launch_count(sl))
+
+
+def dem_slabs_last_error(sl):
+    return lib().dem_slabs_last_error(sl).decode()
+
+
+def dem_slabs_destroy(sl):
+    if sl:
+        lib().dem_slabs_destroy(sl)
+
+
+class Slabs:
+    """One scene as nslabs sub-domains with halo exchange (marshalling only)."""
+
+    def __init__(self, params, x, v, w, r, nslabs, axis=-1, device=0, cuda_stream=None, block_size=0,
+                 max_contacts=0):
+        self.params = params
+        self.n = len(r)
+        self.nslabs = int(nslabs)
+        self.h = dem_slabs_create(config_from_params(params, block_size, max_contacts), nslabs, axis, device,
+                                  cuda_stream)
+        try:
+            dem_slabs_set_walls(self.h, params.walls)
+            dem_slabs_set_particles(self.h, x, v, w, r)
+        except Exception:
+            dem_slabs_destroy(self.h)
+            self.h = None
+            raise
+
+    def step(self, nsteps=1):
+        dem_slabs_step(self.h, nsteps)
+        return self
+
+    def state(self):
+        return dem_slabs_get_state(self.h, self.n)
+
+    def info(self):
+        return dem_slabs_info(self.h, self.nslabs)
+
+    def close(self):
+        if self.h:
+            dem_slabs_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
