@@ -340,7 +340,8 @@ dem_status dem_slabs_create(const dem_config* cfg, int nslabs, int axis, int dev
 /* Walls of the scene, given to every slab (as dem_set_walls). */
 dem_status dem_slabs_set_walls(dem_slabs* s, int nwalls, const dem_wall* walls);
 
-/* Particles of the scene (as dem_set_particles; particle k has id k): the boundaries
+/* Particles of the scene (as dem_set_particles, particle k has id k, n at most
+ * 0x7FFFFF00 / DEM_MAX_SLABS): the boundaries
  * are chosen by dem_slab_bounds over the coordinates along the axis, every particle goes
  * to its owning slab and to the ghost layers that hold it, and every slab sorts. */
 dem_status dem_slabs_set_particles(dem_slabs* s, int64_t n, const double* x, const double* v, const double* w,

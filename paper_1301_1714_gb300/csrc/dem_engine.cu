@@ -1938,7 +1938,9 @@ dem_status dem_slabs_set_particles(dem_slabs* S, int64_t n64, const double* x, c
                                    const float* r, int where) {
     if (!S) return DEM_ERR_INVALID_ARG;
     if (S->broken) return sfail(S, DEM_ERR_STATE, "slabs are unusable after a CUDA error");
-    if (n64 < 0 || n64 > (int64_t)0x7FFFFF00) return sfail(S, DEM_ERR_INVALID_ARG, "n out of range");
+    // every slab holds at most n particles, so the exchange's launch indices over all
+    // slabs (32-bit) cannot overflow
+    if (n64 < 0 || n64 > (int64_t)(0x7FFFFF00 / DEM_MAX_SLABS)) return sfail(S, DEM_ERR_INVALID_ARG, "n out of range");
     if (where != DEM_HOST && where != DEM_DEVICE) return sfail(S, DEM_ERR_INVALID_ARG, "where");
     const uint32_t n = (uint32_t)n64;
     if (n > 0 && (!x || !v || !w || !r)) return sfail(S, DEM_ERR_INVALID_ARG, "x, v, w and r are required");
@@ -1979,6 +1981,7 @@ dem_status dem_slabs_set_particles(dem_slabs* S, int64_t n64, const double* x, c
         S->cur[k] = 0;
     }
     geom.G = S->sl[0]->h;
+    set_keys(geom);
     S->geom = geom;
     S->n = n;
     if (n > S->owner_cap) {

@@ -89,22 +89,23 @@ struct H32 {
     }
 };
 
-// Slab owning coordinate z: the number of interior boundaries at or below z.
-__device__ __forceinline__ int owner_slab(const HaloGeom& g, double z) {
+// Slab owning a coordinate of order key kz: the number of interior boundaries at or
+// below it.
+__device__ __forceinline__ int owner_slab(const HaloGeom& g, uint64_t kz) {
     int o = 0;
 #pragma unroll
     for (int t = 1; t < DEM_MAX_SLABS; ++t)
-        if (t < g.nslabs && z >= g.zb[t]) ++o;
+        if (t < g.nslabs && kz >= g.kb[t]) ++o;
     return o;
 }
 
-// Destinations of a particle at z owned by slab o: bit o, plus bit t for every other
-// slab whose range widened by G on both sides holds z.
-__device__ __forceinline__ uint32_t destinations(const HaloGeom& g, double z, int o) {
+// Destinations of a particle of coordinate key kz owned by slab o: bit o, plus bit t for
+// every other slab whose range widened by G on both sides holds the coordinate.
+__device__ __forceinline__ uint32_t destinations(const HaloGeom& g, uint64_t kz, int o) {
     uint32_t want = 1u << o;
 #pragma unroll
     for (int t = 0; t < DEM_MAX_SLABS; ++t)
-        if (t < g.nslabs && t != o && z >= g.zb[t] - g.G && z < g.zb[t + 1] + g.G) want |= 1u << t;
+        if (t < g.nslabs && t != o && kz >= g.klo[t] && kz < g.khi[t]) want |= 1u << t;
     return want;
 }
 
@@ -193,24 +194,24 @@ __global__ void __launch_bounds__(ROUTE_THREADS, 4) k_halo_route(const __grid_co
         // source position, id and coordinate of every item (loads issued together)
         int sv[ROUTE_ITEMS];
         uint32_t qv[ROUTE_ITEMS], idv[ROUTE_ITEMS];
-        double zv[ROUTE_ITEMS];
+        uint64_t zv[ROUTE_ITEMS];   // order keys of the coordinates
 #pragma unroll
         for (int it = 0; it < ROUTE_ITEMS; ++it) {
             const uint32_t gi = base + it * ROUTE_THREADS + threadIdx.x;
             sv[it] = 0;
             qv[it] = gi;
             idv[it] = gi;
-            zv[it] = 0.0;
+            zv[it] = 0;
             if (gi < a.ntotal) {
                 if (IMPORT) {
-                    zv[it] = a.x[3 * (size_t)gi + a.g.axis];
+                    zv[it] = order_key(a.x[3 * (size_t)gi + a.g.axis]);
                 } else {
                     const int s = source_slab(s_io, S, gi);
                     const uint32_t q = gi - s_io[s].p0;
                     sv[it] = s;
                     qv[it] = q;
                     idv[it] = HP::id(s_io[s].src, q);
-                    zv[it] = HP::coord(s_io[s].src, q, a.g.axis);
+                    zv[it] = order_key(HP::coord(s_io[s].src, q, a.g.axis));
                 }
             }
         }

@@ -41,7 +41,34 @@ struct HaloGeom {
     int32_t axis;                   // 0, 1, 2
     double zb[DEM_MAX_SLABS + 1];   // slab boundaries, zb[0] = -inf, zb[nslabs] = +inf
     double G;                       // ghost width
+    // the same tests as unsigned comparisons of order keys (order_key, set by set_keys):
+    // owner = #{t >= 1 : key(z) >= kb[t]}; ghost of t when klo[t] <= key(z) < khi[t]
+    uint64_t kb[DEM_MAX_SLABS + 1];   // key(zb[t])
+    uint64_t klo[DEM_MAX_SLABS];      // key(zb[t] - G), the difference rounded as a double
+    uint64_t khi[DEM_MAX_SLABS];      // key(zb[t + 1] + G)
 };
+
+// Order key of a double that is not NaN: a <= b exactly when order_key(a) <=
+// order_key(b) (-0 is taken as +0), so the FP64 slab tests become integer comparisons.
+__host__ __device__ inline uint64_t order_key(double d) {
+#ifdef __CUDA_ARCH__
+    uint64_t b = (uint64_t)__double_as_longlong(d);
+#else
+    uint64_t b;
+    static_assert(sizeof(b) == sizeof(d), "64-bit double");
+    __builtin_memcpy(&b, &d, sizeof b);
+#endif
+    if (b == 0x8000000000000000ull) b = 0;
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+inline void set_keys(HaloGeom& g) {
+    for (int t = 0; t <= g.nslabs; ++t) g.kb[t] = order_key(g.zb[t]);
+    for (int t = 0; t < g.nslabs; ++t) {
+        g.klo[t] = order_key(g.zb[t] - g.G);
+        g.khi[t] = order_key(g.zb[t + 1] + g.G);
+    }
+}
 
 // Counters of one exchange (device, zeroed before it).
 struct HaloCounters {
