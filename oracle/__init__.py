@@ -12,6 +12,7 @@ ct, alpha, mu, ksp, kda, ksh, cell_size, domain_lo, domain_hi, walls).
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import math
 import os
@@ -55,33 +56,64 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+def _load(path):
+    """The oracle's C library at `path`, with its argument types declared."""
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    I64 = ctypes.c_int64
+    lib.orc_cell_keys.argtypes = [P, I64, P, P, P]
+    lib.orc_cell_keys.restype = None
+    lib.orc_sort_by_cell.argtypes = [I64, P, P, P]
+    lib.orc_sort_by_cell.restype = ctypes.c_int
+    lib.orc_cell_start.argtypes = [I64, P, I64, P]
+    lib.orc_cell_start.restype = None
+    lib.orc_pairs_brute.argtypes = [I64, P, P, I64, P]
+    lib.orc_pairs_brute.restype = I64
+    lib.orc_pairs_grid.argtypes = [P, I64, P, P, I64, P, P]
+    lib.orc_pairs_grid.restype = I64
+    lib.orc_forces.argtypes = [P, ctypes.c_int32, P, I64, P, P, P, P, P, I64, ctypes.c_int32, P, P, P, I64, P]
+    lib.orc_forces.restype = I64
+    lib.orc_run.argtypes = [P, ctypes.c_int32, P, I64, P, P, P, P, P, P, I64, ctypes.c_int32, I64, P, P, P]
+    lib.orc_run.restype = ctypes.c_int
+    lib.orc_diagnostics.argtypes = [P, I64, P, P, P, P, P]
+    lib.orc_diagnostics.restype = None
+    lib.orc_struct_sizes.argtypes = [P]
+    lib.orc_struct_sizes.restype = None
+    return lib
+
+
 def _L():
     global _lib
     if _lib is None:
         build()
-        lib = ctypes.CDLL(_SO)
-        P = ctypes.c_void_p
-        I64 = ctypes.c_int64
-        lib.orc_cell_keys.argtypes = [P, I64, P, P, P]
-        lib.orc_cell_keys.restype = None
-        lib.orc_sort_by_cell.argtypes = [I64, P, P, P]
-        lib.orc_sort_by_cell.restype = ctypes.c_int
-        lib.orc_cell_start.argtypes = [I64, P, I64, P]
-        lib.orc_cell_start.restype = None
-        lib.orc_pairs_brute.argtypes = [I64, P, P, I64, P]
-        lib.orc_pairs_brute.restype = I64
-        lib.orc_pairs_grid.argtypes = [P, I64, P, P, I64, P, P]
-        lib.orc_pairs_grid.restype = I64
-        lib.orc_forces.argtypes = [P, ctypes.c_int32, P, I64, P, P, P, P, P, I64, ctypes.c_int32, P, P, P, I64, P]
-        lib.orc_forces.restype = I64
-        lib.orc_run.argtypes = [P, ctypes.c_int32, P, I64, P, P, P, P, P, P, I64, ctypes.c_int32, I64, P, P, P]
-        lib.orc_run.restype = ctypes.c_int
-        lib.orc_diagnostics.argtypes = [P, I64, P, P, P, P, P]
-        lib.orc_diagnostics.restype = None
-        lib.orc_struct_sizes.argtypes = [P]
-        lib.orc_struct_sizes.restype = None
-        _lib = lib
+        _lib = _load(_SO)
     return _lib
+
+
+@contextlib.contextmanager
+def variant(source_text, workdir):
+    """Within the block, every oracle call runs a copy of the oracle compiled from
+    `source_text` (a mutated `dem_oracle.c`) in `workdir`. The mutation tests use it to
+    show that a pin fails when a named mistake is planted in the oracle."""
+    global _lib
+    src = os.path.join(str(workdir), "dem_oracle_variant.c")
+    so = os.path.join(str(workdir), "liboracle_variant.so")
+    with open(src, "w") as f:
+        f.write(source_text)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-fno-fast-math", "-o", so, src, "-lm"])
+    saved = _L()
+    _lib = _load(so)
+    try:
+        yield
+    finally:
+        _lib = saved
+
+
+def source():
+    """Text of the oracle's C source."""
+    with open(_SRC) as f:
+        return f.read()
 
 
 def _ptr(a):

@@ -18,7 +18,7 @@
  *   walls .................. Sec. 4.2 step 8                    wall_geometry
  *   update of properties ... Sec. 4.2 step 1                    integrate
  *
- * Readings where the paper is silent or ambiguous (each also listed in the design notes):
+ * Readings where the paper is silent or ambiguous:
  *  - n is the unit vector from particle i to its partner j; v = v_i - v_j; the normal
  *    overlap is delta = r_i + r_j - |x_j - x_i| and delta_n = delta * n, so -k_n delta_n
  *    pushes i away from j (Eq. 4). Contact iff delta > 0, decided as d^2 < R^2 with

@@ -1,8 +1,9 @@
 """Replicas and scene sharding over ranks (one process per GPU).
 
-A single scene is not partitioned across GPUs: that needs a halo exchange of the
-particles near each sub-domain face every step, which this library does not do.
-Independent scenes (a batch, or a stream of requests) are spread over ranks by device
+A single scene is not partitioned across GPUs here. The library can divide one scene
+into slabs with ghost layers and a halo exchange (`dem_slabs_*`), but all slabs of a
+scene live on one device: the transport of the exchanged records between devices is
+not built. Independent scenes (a batch, or a stream of requests) are spread over ranks by device
 memory footprint, and every rank advances its own scenes with no collective in the data
 path. Only host-side figures are reduced: the slowest rank's time and the total
 particle count.

@@ -1,6 +1,6 @@
 """CUDA path against the FP64 oracle, through the C ABI, on the same seeded inputs.
 
-Bars (stated here and in the design notes):
+Bars:
   cell keys, (cell, id) order ............ bit-exact
   contact pair set, FP64 mode ............ bit-exact
   contact pair set, FP32 mode ............ bit-exact outside |d^2 - R^2| <= 2^-36 R^2

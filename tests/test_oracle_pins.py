@@ -475,3 +475,107 @@ def test_diagnostics_closed_forms():
     # L_z = m (x v_y - y v_x) summed + I w_z = M(1*1) + M(0 - 2*3) + 5 I
     assert d[7] == pytest.approx(M * 1 - 6 * M + 5 * I)
     assert d[9] == pytest.approx(2 * M)
+
+
+# ------------------------------------------- parts of Eqs. 1, 5, 7, 8-9 pinned alone
+def test_simple_model_shear_decays_sliding_exponentially():
+    """Eq. 1 on a sphere resting on a plane and sliding along it: v is tangential, so
+    v_t = v and the tangential force is -(k_da + k_sh) v, with no spin (Eq. 1 has no
+    torque). Each semi-implicit Euler step multiplies v by (1 - (k_da + k_sh) dt / m)
+    exactly. A dropped or sign-flipped k_sh term changes the decay rate."""
+    kda, ksh, dt = 0.004, 0.0065, 1e-6
+    p = floor_params(0.3, 0.5, model="simple", ksp=1e4, kda=kda, ksh=ksh, dt=dt)
+    z0 = RF - M * 9.81 / 1e4
+    v0 = 0.05
+    st = oracle.State(p, np.array([[0.0, 0.0, z0]]), np.array([[v0, 0.0, 0.0]]), np.zeros((1, 3)),
+                      np.full(1, R, np.float32))
+    steps = 2000
+    st.run(steps)
+    factor = (1.0 - (kda + ksh) * dt / M) ** steps
+    assert st.v[0, 0] == pytest.approx(v0 * factor, rel=1e-7)
+    assert factor < 0.2
+    assert np.all(st.w == 0.0)
+
+
+def test_hertz_tangential_stiffness_sets_stick_oscillation_period():
+    """Eqs. 8-9: a sphere resting on a plane at its Hertz overlap delta (R_eff = r for a
+    wall) and kicked tangentially, with mu large and no damping, rolls back and forth:
+    the contact point's displacement s obeys s'' = -(k_t/m + k_t r^2/I) s, a period of
+    2 pi sqrt((2m/7) / k_t) with k_t = C_t sqrt(delta r). k_t formed from C_n, or without
+    sqrt(delta r), gives another period."""
+    cn, ct = S.hertz_coeffs(1e4, 2 / 7, R)
+    delta = (M * 9.81 / (cn * math.sqrt(RF))) ** (2.0 / 3.0)
+    kt = ct * math.sqrt(delta * RF)
+    period = 2 * math.pi * math.sqrt((2 * M / 7) / kt)
+    p = floor_params(10.0, 0.5, stiffness="hertz", cn=cn, ct=ct, alpha=0.0, dt=period / 600)
+    st = oracle.State(p, np.array([[0.0, 0.0, RF - delta]]), np.array([[1e-4, 0.0, 0.0]]), np.zeros((1, 3)),
+                      np.full(1, R, np.float32))
+    # slip velocity of the contact point, v_x - r w_y, changes sign every half period
+    prev, crossings = None, []
+    for k in range(int(3.2 * 600)):
+        st.run(1)
+        s = st.v[0, 0] - RF * st.w[0, 1]
+        if prev is not None and (prev > 0) != (s > 0):
+            crossings.append((k + prev / (prev - s)) * p.dt)
+        prev = s
+    assert len(crossings) >= 5
+    measured = 2 * (crossings[4] - crossings[0]) / 4
+    assert measured == pytest.approx(period, rel=5e-3)
+
+
+def _drive(p, x, v, hist, steps):
+    """Evaluate `steps` steps of a kinematically driven state (positions and velocities
+    held, only the springs carried), returning the tangential force on sphere 0 per step."""
+    out = []
+    w = np.zeros_like(x)
+    r = np.full(len(x), R, np.float32)
+    for _ in range(steps):
+        F, _, hist, _ = oracle.forces(p, x, v, w, r, hist)
+        out.append(F[0].copy())
+    return np.array(out), hist
+
+
+def test_spring_after_slip_keeps_eq4_an_identity_on_reversal():
+    """Eq. 5 with the spring reset of the reading taken (after a cap the stored spring is
+    -(F_t + eta v_t)/k_t, so Eq. 4 still gives the capped force). A sphere pressed onto a
+    plane at a fixed overlap is dragged at +u until it slips, then at -u. On the first
+    reversed step Eq. 7 adds -u dt to the spring and the dashpot term flips, so the
+    tangential force jumps from -mu F_n to -mu F_n + 2 eta u + k_t u dt. A reset to
+    -F_t/k_t gives a jump of eta u + k_t u dt; keeping the unbounded spring keeps the force
+    capped at -mu F_n."""
+    e, mu, kn, kt, u, dt = 0.5, 0.3, 1e4, 1e4 * 2 / 7, 0.01, 1e-6
+    p = floor_params(mu, e, g=(0.0, 0.0, 0.0), dt=dt)
+    eta = S.alpha_from_e(e) * math.sqrt(kn * M)
+    delta0 = 1e-6
+    x = np.array([[0.0, 0.0, RF - delta0]])
+    fn = kn * (RF - x[0, 2])
+    F1, hist = _drive(p, x, np.array([[u, 0.0, 0.0]]), oracle.empty_history(), 200)
+    # loading: F_t = -k_t k u dt - eta u until the cap, then -mu F_n
+    assert F1[0, 0] == pytest.approx(-kt * u * dt - eta * u, rel=1e-9)
+    assert F1[-1, 0] == pytest.approx(-mu * fn, rel=1e-9)
+    assert F1[-1, 2] == pytest.approx(fn, rel=1e-9)
+    F2, _ = _drive(p, x, np.array([[-u, 0.0, 0.0]]), hist, 3)
+    jump = 2 * eta * u + kt * u * dt
+    assert F2[0, 0] == pytest.approx(-mu * fn + jump, rel=1e-9)
+    assert F2[1, 0] == pytest.approx(-mu * fn + jump + kt * u * dt, rel=1e-9)
+
+
+def test_history_projection_shrinks_spring_by_cos_theta():
+    """Eq. 7 projects the stored spring onto the new tangent plane without rescaling:
+    when the contact normal turns by theta between steps (and the contact point does not
+    slip), a spring s perpendicular to the old normal and in the plane of the turn keeps
+    length s cos(theta), and the tangential force is -k_t times it."""
+    kt, s, theta = 1e4 * 2 / 7, 2e-7, 0.5
+    p = params(alpha=0.0, mu=0.3)
+    d = 2 * RF - 1e-6
+    x = np.array([[0.0, 0.0, 0.0], [d * math.cos(theta), d * math.sin(theta), 0.0]])
+    hist = oracle.empty_history(1)
+    hist[0] = (0, 1, (0.0, s, 0.0))           # perpendicular to the old normal (1, 0, 0)
+    F, _, h2, _ = oracle.forces(p, x, np.zeros((2, 3)), np.zeros((2, 3)), np.full(2, R, np.float32), hist)
+    assert len(h2) == 1
+    dn = h2[0]["d"]
+    n = x[1] / np.linalg.norm(x[1])
+    assert np.linalg.norm(dn) == pytest.approx(s * math.cos(theta), rel=1e-12)
+    assert abs(np.dot(dn, n)) <= 1e-12 * s
+    Ft = F[0] - np.dot(F[0], n) * n
+    assert np.linalg.norm(Ft) == pytest.approx(kt * s * math.cos(theta), rel=1e-12)
