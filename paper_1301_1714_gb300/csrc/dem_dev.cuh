@@ -15,6 +15,15 @@
 #define DEM_MAX_WALLS 8
 #define DEM_WALL_BASE 0xFFFFFF00u
 
+// Neighbour lists of list mode: a particle lists the candidates of higher global id (it
+// evaluates those pairs, "owned") and keeps a list of the candidates of lower id (its
+// "owners"). An owned entry packs the partner's stored index (27 bits) with the slot
+// the partner reserved for this owner (5 bits).
+#define DEM_NL_SHIFT 27
+#define DEM_NL_INDEX_MASK ((1u << DEM_NL_SHIFT) - 1u)
+#define DEM_LIST_OWNED_CAP 64   // owned entries per particle (one bit each in a 64-bit mask)
+#define DEM_LIST_OWNER_CAP 32   // owners per particle (one bit each in a 32-bit mask)
+
 namespace demgb {
 
 // ------------------------------------------------------------------ scene table
@@ -44,6 +53,9 @@ struct SceneDev {
     float dt_f, g_f[3], kn_f, kt_f, cn_f, ct_f, alpha_f, mu_f, ksp_f, kda_f, ksh_f, cmass_f;
     float eps_f;                // FP32 prefilter margin [m]
     int32_t terms;              // optional force terms (DEM_TERM_*)
+    int32_t bshift;             // cell order: 0 row-major; s > 0 bricks of (2^s)^3 cells (list mode)
+    int32_t bdims[3];           // bricks per axis (bshift > 0)
+    int32_t pad4;
     double mu_roll;             // rolling resistance coefficient
     double alpha_t;             // tangential damping factor
     double kcoh_pi;             // pi * cohesion energy density
@@ -70,7 +82,7 @@ struct StatusDev {
     CountersDev live, last;
 };
 
-enum : int32_t { ST_OK = 0, ST_CAPACITY = 4, ST_NONFINITE = 6 };
+enum : int32_t { ST_OK = 0, ST_CAPACITY = 4, ST_LIST = 5, ST_NONFINITE = 6 };
 
 // Step control, read and written only by kernels (the host never needs to know, while
 // stepping, whether a step sorted).
@@ -86,6 +98,35 @@ struct CtrlDev {
 
 __device__ __forceinline__ void raise_status(StatusDev* st, int32_t code, int32_t where) {
     if (atomicCAS(&st->code, 0, code) == 0) st->where = where;
+}
+
+// Key of cell (i, j, k) of scene S, relative to the scene's first cell. Row-major
+// ((k ny + j) nx + i) or, with bshift = s > 0, bricks of 2^s x 2^s x 2^s cells: bricks in
+// row-major order, cells row-major within their brick. A run of consecutive keys is then
+// a compact block of space, so the particles a thread block holds are mostly each
+// other's neighbours (list mode stores particles in this order).
+__device__ __forceinline__ uint32_t cell_index(const SceneDev& S, uint32_t i, uint32_t j, uint32_t k) {
+    if (S.bshift == 0) return (k * (uint32_t)S.dims[1] + j) * (uint32_t)S.dims[0] + i;
+    const uint32_t sh = (uint32_t)S.bshift, m = (1u << sh) - 1u;
+    const uint32_t brick = ((k >> sh) * (uint32_t)S.bdims[1] + (j >> sh)) * (uint32_t)S.bdims[0] + (i >> sh);
+    return (brick << (3 * sh)) | ((((k & m) << sh) | (j & m)) << sh) | (i & m);
+}
+// Inverse of cell_index.
+__device__ __forceinline__ void cell_coords(const SceneDev& S, uint32_t local, int& i, int& j, int& k) {
+    if (S.bshift == 0) {
+        i = (int)(local % (uint32_t)S.dims[0]);
+        const uint32_t t = local / (uint32_t)S.dims[0];
+        j = (int)(t % (uint32_t)S.dims[1]);
+        k = (int)(t / (uint32_t)S.dims[1]);
+        return;
+    }
+    const uint32_t sh = (uint32_t)S.bshift, m = (1u << sh) - 1u;
+    const uint32_t brick = local >> (3 * sh), in = local & ((1u << (3 * sh)) - 1u);
+    const uint32_t bi = brick % (uint32_t)S.bdims[0], bt = brick / (uint32_t)S.bdims[0];
+    const uint32_t bj = bt % (uint32_t)S.bdims[1], bk = bt / (uint32_t)S.bdims[1];
+    i = (int)((bi << sh) | (in & m));
+    j = (int)((bj << sh) | ((in >> sh) & m));
+    k = (int)((bk << sh) | (in >> (2 * sh)));
 }
 
 // Scene of packed particle index q (scenes are contiguous, in order).

@@ -28,6 +28,8 @@ struct dem_handle {
     double origin[3] = {0, 0, 0};
     double h = 0.0;
     int64_t dims[3] = {1, 1, 1};
+    int bshift = 0;                    // cell order of the sort: 0 row-major, 2 bricks of 4^3 cells (list mode)
+    int64_t bdims[3] = {1, 1, 1};      // bricks per axis
     bool has_particles = false;
     bool broken = false;
     bool eval_valid = false;
@@ -93,7 +95,8 @@ void free_particle_buffers(Domain& d) {
     d.allocations.clear();
     d.S64[0] = d.S64[1] = StateF64{};
     d.S32[0] = d.S32[1] = StateF32{};
-    d.ncnt = d.nl = nullptr;
+    d.ncnt = d.nl = d.ocnt = d.ol = d.inmask = nullptr;
+    d.rec = d.part_sum = nullptr;
     d.ref = nullptr;
     d.canon = d.fin = nullptr;
     for (int i = 0; i < 2; ++i) { d.hcnt[i] = nullptr; d.hpid[i] = nullptr; d.hd[i] = nullptr; }
@@ -192,8 +195,11 @@ void fill_scene(dem_handle* h, SceneDev& S, uint32_t p0, uint32_t np, uint32_t c
     S.p0 = p0;
     S.np = np;
     S.c0 = c0;
-    S.ncell = (uint32_t)(h->dims[0] * h->dims[1] * h->dims[2]);
+    S.bshift = h->bshift;
+    S.ncell = h->bshift ? (uint32_t)((h->bdims[0] * h->bdims[1] * h->bdims[2]) << (3 * h->bshift))
+                        : (uint32_t)(h->dims[0] * h->dims[1] * h->dims[2]);
     for (int a = 0; a < 3; ++a) {
+        S.bdims[a] = (int32_t)h->bdims[a];
         S.dims[a] = (int32_t)h->dims[a];
         S.origin[a] = h->origin[a];
         S.origin_f[a] = (float)h->origin[a];
@@ -299,8 +305,14 @@ dem_status alloc_domain(Domain& d, uint32_t n, uint32_t ncells, std::string& err
     }
     AL(d.key, N * 4); AL(d.rank, N * 4); AL(d.tmp, N * 4); AL(d.perm, N * 4); AL(d.skey, N * 4);
     if (d.list_mode) {
+        const size_t rb = list_record_bytes(d);
         AL(d.ncnt, N * 4);
-        AL(d.nl, N * 4 * (size_t)d.maxn);
+        AL(d.nl, N * 4 * (size_t)DEM_LIST_OWNED_CAP);
+        AL(d.ocnt, N * 4);
+        AL(d.ol, N * 4 * (size_t)DEM_LIST_OWNER_CAP);
+        AL(d.inmask, N * 4);
+        AL(d.rec, N * rb * (size_t)DEM_LIST_OWNER_CAP);
+        AL(d.part_sum, N * rb);
         AL(d.ref, N * 16);
         AL(d.canon, N * 4);
         AL(d.fin, N * 4);
@@ -363,6 +375,13 @@ dem_status sync_status(dem_handle* h) {
                      d.maxc);
             return fail(h, DEM_ERR_CAPACITY, buf);
         }
+        if (code == ST_LIST) {
+            snprintf(buf, sizeof buf,
+                     "neighbour list of the particle at sorted position %d is full (more than %d candidates of "
+                     "higher id or %d of lower id within r_i + r_j + skin); use a smaller skin",
+                     where, DEM_LIST_OWNED_CAP, DEM_LIST_OWNER_CAP);
+            return fail(h, DEM_ERR_CAPACITY, buf);
+        }
         snprintf(buf, sizeof buf, "non-finite position or velocity at sorted position %d", where);
         return fail(h, DEM_ERR_NONFINITE, buf);
     }
@@ -397,8 +416,23 @@ dem_status set_grid(dem_handle* h, bool any, double rmax, int64_t& nc) {
     for (int a = 0; a < 3; ++a) {
         h->origin[a] = c.domain_lo[a];
         h->dims[a] = std::max<int64_t>(1, (int64_t)std::ceil((c.domain_hi[a] - c.domain_lo[a]) / hc));
+        if (h->dims[a] > (int64_t)0x7FFFFFFF) return fail(h, DEM_ERR_INVALID_ARG, "grid has more than 2^31 cells");
         nc *= h->dims[a];
         if (nc > (int64_t)0x7FFFFFFF) return fail(h, DEM_ERR_INVALID_ARG, "grid has more than 2^31 cells");
+    }
+    // list mode numbers cells brick by brick (bricks of 4 x 4 x 4 cells, the grid padded to
+    // whole bricks), so that consecutive stored particles form compact blocks of space
+    h->bshift = h->d.list_mode ? 2 : 0;
+    if (h->bshift) {
+        const int64_t B = (int64_t)1 << h->bshift;
+        nc = 1;
+        for (int a = 0; a < 3; ++a) {
+            h->bdims[a] = (h->dims[a] + B - 1) / B;
+            nc *= h->bdims[a] * B;
+            if (nc > (int64_t)0x7FFFFFFF) return fail(h, DEM_ERR_INVALID_ARG, "grid has more than 2^31 cells");
+        }
+    } else {
+        h->bdims[0] = h->bdims[1] = h->bdims[2] = 1;
     }
     h->h = hc;
     h->rmax = rmax;
@@ -432,6 +466,8 @@ dem_status load_particles(dem_handle* h, int64_t n64, const double* x, const dou
             if (!finite3(x + 3 * (size_t)k) || !finite3(v + 3 * (size_t)k) || !finite3(w + 3 * (size_t)k))
                 return fail(h, DEM_ERR_INVALID_ARG, "non-finite position, velocity or spin in the input");
     const dem_config& c = h->cfg;
+    if (d.list_mode && (uint64_t)n > (uint64_t)DEM_NL_INDEX_MASK + 1)
+        return fail(h, DEM_ERR_INVALID_ARG, "resort_interval != 1 holds at most 2^27 particles");
     int64_t nc = 1;
     dem_status s = set_grid(h, n > 0, rmax, nc);
     if (s != DEM_OK) return s;
@@ -468,6 +504,7 @@ dem_status load_particles(dem_handle* h, int64_t n64, const double* x, const dou
     if (n > 0) {
         CK(h, cudaMemsetAsync(d.hcnt[0], 0, (size_t)n * 4, d.stream));
         CK(h, cudaMemsetAsync(d.hcnt[1], 0, (size_t)n * 4, d.stream));
+        if (d.list_mode) CK(h, cudaMemsetAsync(d.inmask, 0, (size_t)n * 4, d.stream));
         const double *xd = x, *vd = v, *wd = w;
         const float* rd = r;
         if (where == DEM_HOST) {
@@ -705,7 +742,7 @@ dem_status dem_create(const dem_config* cfg, int device, void* cuda_stream, dem_
     d.sort_blocks = sort_blocks_of(device);
     d.list_mode = cfg->resort_interval != 1 ? 1 : 0;
     d.interval = cfg->resort_interval;
-    d.maxn = 2 * d.maxc;
+    d.maxn = DEM_LIST_OWNED_CAP;
     d.stream = (cudaStream_t)cuda_stream;
     if (cudaMalloc(&d.st, sizeof(StatusDev)) != cudaSuccess ||
         cudaMallocHost(&d.st_host, sizeof(StatusDev)) != cudaSuccess ||
@@ -916,6 +953,13 @@ dem_status dem_get_forces(dem_handle* h, double* F, double* T, int where) {
     return sync_status(h);
 }
 
+// Used spring slots of a particle from its count word: in list mode springs are stored
+// once per pair (owned pairs, then walls) and the word is pairs | walls << 16.
+static uint32_t slots_of(const Domain& d, uint32_t raw) {
+    const uint32_t c = d.list_mode ? (raw & 0xFFFFu) + (raw >> 16) : raw;
+    return std::min<uint32_t>(c, (uint32_t)d.maxc);
+}
+
 static dem_status download_u32(dem_handle* h, std::vector<uint32_t>& out, const uint32_t* src, size_t count) {
     out.resize(count);
     if (count) CK(h, cudaMemcpyAsync(out.data(), src, count * 4, cudaMemcpyDeviceToHost, h->d.stream));
@@ -942,7 +986,7 @@ dem_status dem_get_history(dem_handle* h, int64_t cap, uint32_t* oi, uint32_t* o
     if (!ctl.perm_valid)
         for (size_t q = 0; q < n; ++q) perm[q] = (uint32_t)q;
     uint32_t mx = 0;
-    for (size_t q = 0; q < n; ++q) mx = std::max(mx, std::min<uint32_t>(cnt[perm[q]], (uint32_t)M));
+    for (size_t q = 0; q < n; ++q) mx = std::max(mx, slots_of(d, cnt[perm[q]]));
     std::vector<uint32_t> pid((size_t)mx * N);
     std::vector<double> dv((size_t)3 * mx * N);
     if (mx) {
@@ -965,7 +1009,7 @@ dem_status dem_get_history(dem_handle* h, int64_t cap, uint32_t* oi, uint32_t* o
     std::vector<Rec> recs;
     for (size_t q = 0; q < n; ++q) {
         const uint32_t src = perm[q], owner = ids[q];
-        const uint32_t c = std::min<uint32_t>(cnt[src], (uint32_t)M);
+        const uint32_t c = slots_of(d, cnt[src]);
         for (uint32_t k = 0; k < c; ++k) {
             const uint32_t p = pid[(size_t)k * N + src];
             if (p >= DEM_WALL_BASE || owner < p) {
@@ -999,7 +1043,7 @@ dem_status dem_restore(dem_handle* h, int64_t n, const double* x, const double* 
     }
     // per-particle lists in id order; after the first sort perm[q] is the id position
     const size_t N = d.cap, M = d.maxc;
-    std::vector<uint32_t> cnt(N, 0), pid(M * N, 0);
+    std::vector<uint32_t> cnt(N, 0), pid(M * N, 0), npairs;
     std::vector<double> dv(3 * M * N, 0.0);
     auto add = [&](uint32_t owner, uint32_t partner, double a, double b, double c) -> bool {
         if (owner >= (uint32_t)n) return false;
@@ -1013,14 +1057,26 @@ dem_status dem_restore(dem_handle* h, int64_t n, const double* x, const double* 
         return true;
     };
     const int nw = (int)h->walls.size();
-    for (int64_t k = 0; k < nrec; ++k) {
-        const uint32_t i = ri[k], j = rj[k];
-        const double* dd = rd + 3 * k;
-        bool ok;
-        if (j >= DEM_WALL_BASE) ok = (int)(j - DEM_WALL_BASE) < nw && add(i, j, dd[0], dd[1], dd[2]);
-        else ok = i < j && j < (uint32_t)n && add(i, j, dd[0], dd[1], dd[2]) && add(j, i, -dd[0], -dd[1], -dd[2]);
-        if (!ok) { h->has_particles = false; return fail(h, DEM_ERR_INVALID_ARG, "invalid or excess history record"); }
+    // walk mode: each pair's spring on both sides (the partner's is the negative), walls
+    // in record order. List mode: each pair's spring once, on the lower id's side, the
+    // walls after the pairs, and the count word pairs | walls << 16.
+    const bool once = d.list_mode != 0;
+    for (int pass = 0; pass < (once ? 2 : 1); ++pass) {
+        for (int64_t k = 0; k < nrec; ++k) {
+            const uint32_t i = ri[k], j = rj[k];
+            const double* dd = rd + 3 * k;
+            const bool wall = j >= DEM_WALL_BASE;
+            if (once && wall != (pass == 1)) continue;
+            bool ok;
+            if (wall) ok = (int)(j - DEM_WALL_BASE) < nw && add(i, j, dd[0], dd[1], dd[2]);
+            else ok = i < j && j < (uint32_t)n && add(i, j, dd[0], dd[1], dd[2]) &&
+                      (once || add(j, i, -dd[0], -dd[1], -dd[2]));
+            if (!ok) { h->has_particles = false; return fail(h, DEM_ERR_INVALID_ARG, "invalid or excess history record"); }
+        }
+        if (once && pass == 0) npairs = cnt;
     }
+    if (once)
+        for (size_t q = 0; q < (size_t)n; ++q) cnt[q] = npairs[q] | ((cnt[q] - npairs[q]) << 16);
     CK(h, cudaMemcpyAsync(d.hcnt[d.h_cur], cnt.data(), N * 4, cudaMemcpyHostToDevice, d.stream));
     CK(h, cudaMemcpyAsync(d.hpid[d.h_cur], pid.data(), M * N * 4, cudaMemcpyHostToDevice, d.stream));
     if (d.precision == 0) {
@@ -1060,6 +1116,17 @@ dem_status dem_get_diagnostics(dem_handle* h, double* out) {
     return DEM_OK;
 }
 
+// Row-major key ((k ny + j) nx + i) of a cell key of the handle's sort order.
+static uint32_t row_major_key(const dem_handle* h, uint32_t key) {
+    if (h->bshift == 0) return key;
+    const uint32_t sh = (uint32_t)h->bshift, m = (1u << sh) - 1u;
+    const uint32_t brick = key >> (3 * sh), in = key & ((1u << (3 * sh)) - 1u);
+    const uint32_t bi = brick % (uint32_t)h->bdims[0], bt = brick / (uint32_t)h->bdims[0];
+    const uint32_t bj = bt % (uint32_t)h->bdims[1], bk = bt / (uint32_t)h->bdims[1];
+    const uint32_t i = (bi << sh) | (in & m), j = (bj << sh) | ((in >> sh) & m), k = (bk << sh) | (in >> (2 * sh));
+    return (uint32_t)(((uint64_t)k * (uint64_t)h->dims[1] + j) * (uint64_t)h->dims[0] + i);
+}
+
 dem_status dem_debug_snapshot(dem_handle* h, uint32_t* cell, uint32_t* order, int64_t pair_cap, uint32_t* pairs,
                               int64_t* npairs) {
     if (!h) return DEM_ERR_INVALID_ARG;
@@ -1075,6 +1142,8 @@ dem_status dem_debug_snapshot(dem_handle* h, uint32_t* cell, uint32_t* order, in
     if ((s = download_u32(h, ids, d.precision == 0 ? d.S64[ctl.cur].id : d.S32[ctl.cur].id, n)) != DEM_OK) return s;
     if ((s = download_u32(h, skey, d.skey, n)) != DEM_OK) return s;
     CK(h, cudaStreamSynchronize(d.stream));
+    // keys in row-major numbering ((k ny + j) nx + i), whatever order the sort used
+    for (size_t q = 0; q < n; ++q) skey[q] = row_major_key(h, skey[q]);
     if (cell)
         for (size_t q = 0; q < n; ++q) cell[ids[q]] = skey[q];
     if (order) {
@@ -1096,7 +1165,7 @@ dem_status dem_debug_snapshot(dem_handle* h, uint32_t* cell, uint32_t* order, in
         if ((s = download_u32(h, cnt, d.hcnt[ho], n)) != DEM_OK) return s;
         CK(h, cudaStreamSynchronize(d.stream));
         uint32_t mx = 0;
-        for (size_t q = 0; q < n; ++q) mx = std::max(mx, std::min<uint32_t>(cnt[q], (uint32_t)d.maxc));
+        for (size_t q = 0; q < n; ++q) mx = std::max(mx, slots_of(d, cnt[q]));
         std::vector<uint32_t> pid((size_t)mx * N);
         if (mx) {
             CK(h, cudaMemcpyAsync(pid.data(), d.hpid[ho], (size_t)mx * N * 4, cudaMemcpyDeviceToHost, d.stream));
@@ -1104,7 +1173,7 @@ dem_status dem_debug_snapshot(dem_handle* h, uint32_t* cell, uint32_t* order, in
         }
         std::vector<std::pair<uint32_t, uint32_t>> pr;
         for (size_t q = 0; q < n; ++q) {
-            const uint32_t c = std::min<uint32_t>(cnt[q], (uint32_t)d.maxc);
+            const uint32_t c = slots_of(d, cnt[q]);
             for (uint32_t k = 0; k < c; ++k) {
                 const uint32_t p = pid[(size_t)k * N + q];
                 if (p < DEM_WALL_BASE && ids[q] < p) pr.emplace_back(ids[q], p);
@@ -1140,7 +1209,9 @@ int64_t dem_device_bytes(const dem_handle* h) {
     size_t b = 2 * state + 2 * (N * 4 + N * 4 * M + N * T * 3 * M) + 5 * N * 4 + 2 * C * 4 + (size_t)d.part_cap * 4 +
                (size_t)d.diag_part_cap * 80 + sizeof(StatusDev) + 128 + sizeof(SceneDev) * d.scenes_cap;
     b += (size_t)h->stage_cap * (9 * 8 + 4);
-    if (d.list_mode) b += N * (4 + 4 * (size_t)d.maxn + 16 + 8);
+    if (d.list_mode)
+        b += N * (3 * 4 + 4 * (size_t)(DEM_LIST_OWNED_CAP + DEM_LIST_OWNER_CAP) + 16 + 8 +
+                  list_record_bytes(d) * (DEM_LIST_OWNER_CAP + 1));
     return (int64_t)b;
 }
 
@@ -1438,7 +1509,7 @@ dem_status dem_batch_create(int precision, int model, int stiffness, int max_con
     d.model = model;
     d.stiffness = stiffness;
     d.maxc = max_contacts > 0 ? max_contacts : 32;
-    d.maxn = 2 * d.maxc;
+    d.maxn = DEM_LIST_OWNED_CAP;
     d.block = block_size > 0 ? block_size : 256;
     d.sort_blocks = sort_blocks_of(device);
     d.stream = (cudaStream_t)cuda_stream;

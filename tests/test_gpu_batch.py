@@ -117,10 +117,14 @@ def test_list_mode_graph_with_conditional_sort_equals_plain_launches(torch_cuda,
     for u, w in zip(a, b):
         assert np.array_equal(u, w)
     assert sa == sb and sa >= 3
-    # plain: 11 kernels per step; graph: force, condition and bookkeeping per step plus
-    # the 9 sort kernels of each sort that ran (the last, odd step runs plain: 11)
-    assert la == 241 * 11
-    assert lb == 240 * 3 + 11 + 9 * sa or lb == 240 * 3 + 11 + 9 * (sa - 1)
+    # plain: 13 kernels per step (pair pass, update, 10 sort kernels that return early
+    # when the step does not sort, bookkeeping); graph: pair pass, update, condition and
+    # bookkeeping per step plus the 10 sort kernels of each sort that ran (the last, odd
+    # step runs plain: 13)
+    force, body = 2, 10
+    plain = force + body + 1
+    assert la == 241 * plain
+    assert lb == 240 * (force + 2) + plain + body * sa or lb == 240 * (force + 2) + plain + body * (sa - 1)
     # phase timing on a stream: force pass plain, the sort tail as a small graph per step
     with dem.Simulation(p, sc.x, v, sc.w, sc.r, cuda_stream=stream.cuda_stream) as s:
         dem.dem_set_timing(s.h, True)
@@ -131,7 +135,7 @@ def test_list_mode_graph_with_conditional_sort_equals_plain_launches(torch_cuda,
         c = s.state()
     for u, w in zip(a, c):
         assert np.array_equal(u, w)
-    assert lt == 241 * 3 + 9 * sa
+    assert lt == 241 * (force + 2) + body * sa
     assert ph[0] > 0 and ph[1] > 0 and ph[2] == 241 and ph[3] == 241
 
 
