@@ -15,14 +15,13 @@
 #define DEM_MAX_WALLS 8
 #define DEM_WALL_BASE 0xFFFFFF00u
 
-// Neighbour lists of list mode: a particle lists the candidates of higher global id (it
-// evaluates those pairs, "owned") and keeps a list of the candidates of lower id (its
-// "owners"). An owned entry packs the partner's stored index (27 bits) with the slot
-// the partner reserved for this owner (5 bits).
-#define DEM_NL_SHIFT 27
-#define DEM_NL_INDEX_MASK ((1u << DEM_NL_SHIFT) - 1u)
-#define DEM_LIST_OWNED_CAP 64   // owned entries per particle (one bit each in a 64-bit mask)
-#define DEM_LIST_OWNER_CAP 32   // owners per particle (one bit each in a 32-bit mask)
+// Neighbour lists of list mode: at most DEM_LIST_CAP candidates per particle (one bit each
+// in the force pass's 64-bit mask); a fuller list is reported, never truncated silently.
+#define DEM_LIST_CAP 64
+// Cell order of list mode: bricks of 2^s x 2^s x 2^s cells (0 = row-major).
+#ifndef DEM_LIST_BRICK_SHIFT
+#define DEM_LIST_BRICK_SHIFT 2
+#endif
 
 namespace demgb {
 

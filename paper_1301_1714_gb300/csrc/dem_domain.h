@@ -46,25 +46,15 @@ struct Domain {
     CtrlDev* ctrl_host = nullptr;  // pinned copy
 
     // neighbour lists (list mode: resort_interval != 1): candidates within r_i + r_j + skin
-    // of each particle at the last sort, split by global id. Owned (higher id) entries are
-    // slot-major nl[k*cap + q] (partner index | reserved slot << DEM_NL_SHIFT), counts
-    // ncnt[q]; owners (lower id) ol[s*cap + q], counts ocnt[q] (used while building).
+    // of each particle at the last sort, slot-major nl[k*cap + q], counts ncnt[q]
     int list_mode = 0;
-    int maxn = DEM_LIST_OWNED_CAP;
+    int maxn = DEM_LIST_CAP;
     int interval = 1;              // sort at least every `interval` steps (0 = skin only)
     float skin_f = 0.f;            // skin [m]
     float thresh2 = 0.f;           // squared displacement that forces a sort
     uint32_t* ncnt = nullptr;
     uint32_t* nl = nullptr;
     float4* ref = nullptr;         // positions at the last sort
-    uint32_t* ocnt = nullptr;
-    uint32_t* ol = nullptr;
-    // pair-once force pass: the owner of a contact writes the partner's share into the
-    // partner's reserved record slot rec[s*cap + q] (slot-major) and sets bit s of
-    // inmask[q]; part_sum[q] holds each particle's sums over its owned contacts
-    uint32_t* inmask = nullptr;
-    void* rec = nullptr;
-    void* part_sum = nullptr;
     uint32_t* canon = nullptr;     // (cell, id) position -> pre-sort position, at a sort
     uint32_t* fin = nullptr;       // (cell, id) position -> stored position (window order by contact count)
 
@@ -123,10 +113,9 @@ cudaError_t run_rebuild(Domain& d);   // scan, scatter, (cell, id) gather, lists
 cudaError_t run_end_step(Domain& d);  // step bookkeeping (swap or keep, counters)
 cudaError_t run_sort_cond(Domain& d, cudaGraphConditionalHandle h);  // graph condition = this step sorts
 cudaError_t run_force(Domain& d, bool eval, double* dbgF, double* dbgT);
-// list mode (dem_list.cu): the lists of a sort, and the pair-once force pass
+// list mode (dem_list.cu): the neighbour lists of a sort, and the force pass over them
 cudaError_t run_lists(Domain& d);
 cudaError_t run_force_list(Domain& d, bool eval, double* dbgF, double* dbgT);
-size_t list_record_bytes(const Domain& d);   // bytes of one contact record
 cudaError_t run_export(Domain& d, double* x, double* v, double* w);
 cudaError_t run_diag(Domain& d);   // fills d.diag_out[0..9] (device)
 // batches: springs into sorted order (into the free history buffer), new packed layout,

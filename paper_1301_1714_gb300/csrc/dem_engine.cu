@@ -95,8 +95,7 @@ void free_particle_buffers(Domain& d) {
     d.allocations.clear();
     d.S64[0] = d.S64[1] = StateF64{};
     d.S32[0] = d.S32[1] = StateF32{};
-    d.ncnt = d.nl = d.ocnt = d.ol = d.inmask = nullptr;
-    d.rec = d.part_sum = nullptr;
+    d.ncnt = d.nl = nullptr;
     d.ref = nullptr;
     d.canon = d.fin = nullptr;
     for (int i = 0; i < 2; ++i) { d.hcnt[i] = nullptr; d.hpid[i] = nullptr; d.hd[i] = nullptr; }
@@ -305,14 +304,8 @@ dem_status alloc_domain(Domain& d, uint32_t n, uint32_t ncells, std::string& err
     }
     AL(d.key, N * 4); AL(d.rank, N * 4); AL(d.tmp, N * 4); AL(d.perm, N * 4); AL(d.skey, N * 4);
     if (d.list_mode) {
-        const size_t rb = list_record_bytes(d);
         AL(d.ncnt, N * 4);
-        AL(d.nl, N * 4 * (size_t)DEM_LIST_OWNED_CAP);
-        AL(d.ocnt, N * 4);
-        AL(d.ol, N * 4 * (size_t)DEM_LIST_OWNER_CAP);
-        AL(d.inmask, N * 4);
-        AL(d.rec, N * rb * (size_t)DEM_LIST_OWNER_CAP);
-        AL(d.part_sum, N * rb);
+        AL(d.nl, N * 4 * (size_t)DEM_LIST_CAP);
         AL(d.ref, N * 16);
         AL(d.canon, N * 4);
         AL(d.fin, N * 4);
@@ -377,9 +370,9 @@ dem_status sync_status(dem_handle* h) {
         }
         if (code == ST_LIST) {
             snprintf(buf, sizeof buf,
-                     "neighbour list of the particle at sorted position %d is full (more than %d candidates of "
-                     "higher id or %d of lower id within r_i + r_j + skin); use a smaller skin",
-                     where, DEM_LIST_OWNED_CAP, DEM_LIST_OWNER_CAP);
+                     "neighbour list of the particle at sorted position %d is full (more than %d candidates "
+                     "within r_i + r_j + skin); use a smaller skin",
+                     where, DEM_LIST_CAP);
             return fail(h, DEM_ERR_CAPACITY, buf);
         }
         snprintf(buf, sizeof buf, "non-finite position or velocity at sorted position %d", where);
@@ -422,7 +415,7 @@ dem_status set_grid(dem_handle* h, bool any, double rmax, int64_t& nc) {
     }
     // list mode numbers cells brick by brick (bricks of 4 x 4 x 4 cells, the grid padded to
     // whole bricks), so that consecutive stored particles form compact blocks of space
-    h->bshift = h->d.list_mode ? 2 : 0;
+    h->bshift = h->d.list_mode ? DEM_LIST_BRICK_SHIFT : 0;
     if (h->bshift) {
         const int64_t B = (int64_t)1 << h->bshift;
         nc = 1;
@@ -466,8 +459,6 @@ dem_status load_particles(dem_handle* h, int64_t n64, const double* x, const dou
             if (!finite3(x + 3 * (size_t)k) || !finite3(v + 3 * (size_t)k) || !finite3(w + 3 * (size_t)k))
                 return fail(h, DEM_ERR_INVALID_ARG, "non-finite position, velocity or spin in the input");
     const dem_config& c = h->cfg;
-    if (d.list_mode && (uint64_t)n > (uint64_t)DEM_NL_INDEX_MASK + 1)
-        return fail(h, DEM_ERR_INVALID_ARG, "resort_interval != 1 holds at most 2^27 particles");
     int64_t nc = 1;
     dem_status s = set_grid(h, n > 0, rmax, nc);
     if (s != DEM_OK) return s;
@@ -504,7 +495,6 @@ dem_status load_particles(dem_handle* h, int64_t n64, const double* x, const dou
     if (n > 0) {
         CK(h, cudaMemsetAsync(d.hcnt[0], 0, (size_t)n * 4, d.stream));
         CK(h, cudaMemsetAsync(d.hcnt[1], 0, (size_t)n * 4, d.stream));
-        if (d.list_mode) CK(h, cudaMemsetAsync(d.inmask, 0, (size_t)n * 4, d.stream));
         const double *xd = x, *vd = v, *wd = w;
         const float* rd = r;
         if (where == DEM_HOST) {
@@ -742,7 +732,7 @@ dem_status dem_create(const dem_config* cfg, int device, void* cuda_stream, dem_
     d.sort_blocks = sort_blocks_of(device);
     d.list_mode = cfg->resort_interval != 1 ? 1 : 0;
     d.interval = cfg->resort_interval;
-    d.maxn = DEM_LIST_OWNED_CAP;
+    d.maxn = DEM_LIST_CAP;
     d.stream = (cudaStream_t)cuda_stream;
     if (cudaMalloc(&d.st, sizeof(StatusDev)) != cudaSuccess ||
         cudaMallocHost(&d.st_host, sizeof(StatusDev)) != cudaSuccess ||
@@ -953,12 +943,8 @@ dem_status dem_get_forces(dem_handle* h, double* F, double* T, int where) {
     return sync_status(h);
 }
 
-// Used spring slots of a particle from its count word: in list mode springs are stored
-// once per pair (owned pairs, then walls) and the word is pairs | walls << 16.
-static uint32_t slots_of(const Domain& d, uint32_t raw) {
-    const uint32_t c = d.list_mode ? (raw & 0xFFFFu) + (raw >> 16) : raw;
-    return std::min<uint32_t>(c, (uint32_t)d.maxc);
-}
+// Used spring slots of a particle from its count word.
+static uint32_t slots_of(const Domain& d, uint32_t raw) { return std::min<uint32_t>(raw, (uint32_t)d.maxc); }
 
 static dem_status download_u32(dem_handle* h, std::vector<uint32_t>& out, const uint32_t* src, size_t count) {
     out.resize(count);
@@ -1043,7 +1029,7 @@ dem_status dem_restore(dem_handle* h, int64_t n, const double* x, const double* 
     }
     // per-particle lists in id order; after the first sort perm[q] is the id position
     const size_t N = d.cap, M = d.maxc;
-    std::vector<uint32_t> cnt(N, 0), pid(M * N, 0), npairs;
+    std::vector<uint32_t> cnt(N, 0), pid(M * N, 0);
     std::vector<double> dv(3 * M * N, 0.0);
     auto add = [&](uint32_t owner, uint32_t partner, double a, double b, double c) -> bool {
         if (owner >= (uint32_t)n) return false;
@@ -1057,26 +1043,14 @@ dem_status dem_restore(dem_handle* h, int64_t n, const double* x, const double* 
         return true;
     };
     const int nw = (int)h->walls.size();
-    // walk mode: each pair's spring on both sides (the partner's is the negative), walls
-    // in record order. List mode: each pair's spring once, on the lower id's side, the
-    // walls after the pairs, and the count word pairs | walls << 16.
-    const bool once = d.list_mode != 0;
-    for (int pass = 0; pass < (once ? 2 : 1); ++pass) {
-        for (int64_t k = 0; k < nrec; ++k) {
-            const uint32_t i = ri[k], j = rj[k];
-            const double* dd = rd + 3 * k;
-            const bool wall = j >= DEM_WALL_BASE;
-            if (once && wall != (pass == 1)) continue;
-            bool ok;
-            if (wall) ok = (int)(j - DEM_WALL_BASE) < nw && add(i, j, dd[0], dd[1], dd[2]);
-            else ok = i < j && j < (uint32_t)n && add(i, j, dd[0], dd[1], dd[2]) &&
-                      (once || add(j, i, -dd[0], -dd[1], -dd[2]));
-            if (!ok) { h->has_particles = false; return fail(h, DEM_ERR_INVALID_ARG, "invalid or excess history record"); }
-        }
-        if (once && pass == 0) npairs = cnt;
+    for (int64_t k = 0; k < nrec; ++k) {
+        const uint32_t i = ri[k], j = rj[k];
+        const double* dd = rd + 3 * k;
+        bool ok;
+        if (j >= DEM_WALL_BASE) ok = (int)(j - DEM_WALL_BASE) < nw && add(i, j, dd[0], dd[1], dd[2]);
+        else ok = i < j && j < (uint32_t)n && add(i, j, dd[0], dd[1], dd[2]) && add(j, i, -dd[0], -dd[1], -dd[2]);
+        if (!ok) { h->has_particles = false; return fail(h, DEM_ERR_INVALID_ARG, "invalid or excess history record"); }
     }
-    if (once)
-        for (size_t q = 0; q < (size_t)n; ++q) cnt[q] = npairs[q] | ((cnt[q] - npairs[q]) << 16);
     CK(h, cudaMemcpyAsync(d.hcnt[d.h_cur], cnt.data(), N * 4, cudaMemcpyHostToDevice, d.stream));
     CK(h, cudaMemcpyAsync(d.hpid[d.h_cur], pid.data(), M * N * 4, cudaMemcpyHostToDevice, d.stream));
     if (d.precision == 0) {
@@ -1209,9 +1183,7 @@ int64_t dem_device_bytes(const dem_handle* h) {
     size_t b = 2 * state + 2 * (N * 4 + N * 4 * M + N * T * 3 * M) + 5 * N * 4 + 2 * C * 4 + (size_t)d.part_cap * 4 +
                (size_t)d.diag_part_cap * 80 + sizeof(StatusDev) + 128 + sizeof(SceneDev) * d.scenes_cap;
     b += (size_t)h->stage_cap * (9 * 8 + 4);
-    if (d.list_mode)
-        b += N * (3 * 4 + 4 * (size_t)(DEM_LIST_OWNED_CAP + DEM_LIST_OWNER_CAP) + 16 + 8 +
-                  list_record_bytes(d) * (DEM_LIST_OWNER_CAP + 1));
+    if (d.list_mode) b += N * (4 + 4 * (size_t)DEM_LIST_CAP + 16 + 8);
     return (int64_t)b;
 }
 
@@ -1509,7 +1481,7 @@ dem_status dem_batch_create(int precision, int model, int stiffness, int max_con
     d.model = model;
     d.stiffness = stiffness;
     d.maxc = max_contacts > 0 ? max_contacts : 32;
-    d.maxn = DEM_LIST_OWNED_CAP;
+    d.maxn = DEM_LIST_CAP;
     d.block = block_size > 0 ? block_size : 256;
     d.sort_blocks = sort_blocks_of(device);
     d.stream = (cudaStream_t)cuda_stream;

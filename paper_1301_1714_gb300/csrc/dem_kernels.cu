@@ -433,7 +433,7 @@ __global__ void k_rank_cell(uint32_t n, typename PR::State S0, typename PR::Stat
         uint32_t r = 0;
         for (uint32_t k = lo; k < hi; ++k) r += (B.id[tmp[k]] < idp) ? 1u : 0u;
         canon[lo + r] = p;
-        wkey[lo + r] = hcnt_last[p] & 0xFFFFu;   // contacts this particle evaluated (owned pairs)
+        wkey[lo + r] = hcnt_last[p];
     }
 }
 

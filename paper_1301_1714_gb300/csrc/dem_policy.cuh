@@ -69,7 +69,7 @@ struct PF64 {
                                                          const uint32_t* nl, uint32_t m, size_t cap, uint32_t q) {
         uint64_t mask = 0;
         for (uint32_t k = 0; k < m; ++k) {
-            const uint32_t j = __ldg(&nl[k * cap + q]) & DEM_NL_INDEX_MASK;
+            const uint32_t j = __ldg(&nl[k * cap + q]);
             if (touches(me, __ldg(&s.x[j]), __ldg(&s.y[j]), __ldg(&s.z[j]), __ldg(&s.r[j]))) mask |= 1ull << k;
         }
         return mask;
@@ -295,14 +295,14 @@ struct PF32 {
         // (no L1 prefetch of the near candidates' payload: measured 9% slower here and 4%
         // in the walk; the prefetched lines are evicted before phase 2 reads them)
         for (; k + 2 <= m; k += 2) {
-            const uint32_t j0 = __ldg(&nl[k * cap + q]) & DEM_NL_INDEX_MASK;
-            const uint32_t j1 = __ldg(&nl[(k + 1) * cap + q]) & DEM_NL_INDEX_MASK;
+            const uint32_t j0 = __ldg(&nl[k * cap + q]);
+            const uint32_t j1 = __ldg(&nl[(k + 1) * cap + q]);
             const float4 a = __ldg(&s.P0[j0]), b = __ldg(&s.P0[j1]);
             if (near(me, a, eps)) mask |= 1ull << k;
             if (near(me, b, eps)) mask |= 1ull << (k + 1);
         }
         if (k < m) {
-            const uint32_t j0 = __ldg(&nl[k * cap + q]) & DEM_NL_INDEX_MASK;
+            const uint32_t j0 = __ldg(&nl[k * cap + q]);
             if (near(me, __ldg(&s.P0[j0]), eps)) mask |= 1ull << k;
         }
         return mask;

@@ -117,11 +117,10 @@ def test_list_mode_graph_with_conditional_sort_equals_plain_launches(torch_cuda,
     for u, w in zip(a, b):
         assert np.array_equal(u, w)
     assert sa == sb and sa >= 3
-    # plain: 13 kernels per step (pair pass, update, 10 sort kernels that return early
-    # when the step does not sort, bookkeeping); graph: pair pass, update, condition and
-    # bookkeeping per step plus the 10 sort kernels of each sort that ran (the last, odd
-    # step runs plain: 13)
-    force, body = 2, 10
+    # plain: 11 kernels per step (force pass, 9 sort kernels that return early when the
+    # step does not sort, bookkeeping); graph: force pass, condition and bookkeeping per
+    # step plus the 9 sort kernels of each sort that ran (the last, odd step runs plain)
+    force, body = 1, 9
     plain = force + body + 1
     assert la == 241 * plain
     assert lb == 240 * (force + 2) + plain + body * sa or lb == 240 * (force + 2) + plain + body * (sa - 1)
