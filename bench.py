@@ -5,18 +5,24 @@ Workload (default `drum`): 4,194,304 spheres, radii U[0.9, 1.1] mm, dense bed in
 of radius 300 mean radii and length 208 mean radii rotating at 2 rad/s about its
 horizontal axis, mu = 0.5, e = 0.7, practical model (Eqs. 2-10), linear stiffness
 k_n = 1e4 N/m, k_t = (2/7) k_n, dt = contact time of the smallest pair / 50, FP32
-forces with compensated positions, cell sort every step (Sec. 4.2). The bed is built by
-the seeded deposition generator and settled on the GPU for `--settle` steps before the
-warm-up; the working set (about 1.7 GB) is far larger than L2, so no flush is needed.
+forces with compensated positions. The sort policy and block size are chosen by the
+autotuner: in practice the cell sort (Sec. 4.2 steps 2-4) runs only after some particle
+has moved half a skin, with neighbour lists built at each sort (sorting every step, as
+the paper does, is measured beside it). The bed is built by the seeded deposition
+generator and settled on the GPU for `--settle` steps before the warm-up; the working
+set (several GB) is far larger than L2, so no flush is needed.
 
-One benchmark step is one timestep of the whole path: force pass (steps 5-8 and 1, with
-the new cell map of step 2) and cell sort (steps 3-4).
+One benchmark step is one timestep of the whole path: the force pass (steps 5-8 and 1)
+and, on the steps that sort, the cell sort and new lists. Because a short timed window
+may hold no sort, the line also reports an amortized rate over a longer window with the
+measured number of steps per sort.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the CPU oracle (the FP64 C statement of the method, one core) on
-a bounded sample of the same workload. Under torchrun every rank runs an independent
-replica (replicas only: a single scene is not partitioned across GPUs); rank 0 prints.
+a bounded sample of the same workload. With N > 1 every rank runs an independent replica
+(replicas only: a single scene is not partitioned across GPUs); without torchrun,
+--gpus N launches the N ranks itself. Rank 0 prints.
 """
 from __future__ import annotations
 
@@ -68,6 +74,14 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--cpu-procs", type=int, default=0,
+                    help="oracle processes of the all-cores baseline (0 = every host core, -1 = skip)")
+    ap.add_argument("--amortize-steps", type=int, default=1000,
+                    help="steps of the window that measures the steps per sort and the amortized rate (0 = skip)")
+    ap.add_argument("--config2-steps", type=int, default=300,
+                    help="timed steps of each mode on the 262,144-sphere polydisperse bed (0 = skip)")
+    ap.add_argument("--config2-check-steps", type=int, default=50,
+                    help="steps compared with the FP64 oracle on that bed")
     ap.add_argument("--batch-scenes", type=int, default=256, help="scenes of the batched run (0 = skip)")
     ap.add_argument("--batch-steps", type=int, default=300)
     ap.add_argument("--batch-seq-scenes", type=int, default=32, help="scenes timed one by one for comparison")
@@ -180,6 +194,58 @@ def run_batch_bench(args, dem, dev_index, stream, block=0):
             "sequential_sample": f"first {min(args.batch_seq_scenes, len(mix))} scenes, one handle each, "
                                  f"{args.batch_steps} steps",
             "batched_over_sequential": round(batched / seq, 2) if seq else None}
+
+
+def run_config2(args, dem, dev_index, stream):
+    """The 262,144-sphere polydisperse bed (r ~ U[0.8, 1.2] mm, random loose fill in a box
+    of 160 x 160 x 400 mean radii) settling under gravity: throughput of the practical
+    model with FP32 forces (compensated positions) and in FP64, and of the simple model
+    (Eq. 1), each sorting only after a particle moved half a skin of 0.1 r_max; and each
+    mode's distance from the FP64 oracle after `config2_check_steps` steps from the same
+    start (the oracle runs the whole bed, one core)."""
+    import torch
+    import oracle
+    from paper_1301_1714_gb300 import scenes
+    sc = scenes.box_rsa(seed=args.seed, n=262_144, precision="fp32")
+    skin = 0.1 * float(sc.r.max())
+    listed = lambda q: q.copy(resort_interval=0, skin=skin, cell_size=q.cell_size + skin)
+    modes = {"fp32_practical": listed(sc.params), "fp64_practical": listed(sc.params.copy(precision="fp64")),
+             "fp32_simple": listed(sc.params.copy(model="simple")), "fp64_simple": listed(
+                 sc.params.copy(model="simple", precision="fp64"))}
+    ksteps = args.config2_check_steps
+    t0 = time.perf_counter()
+    refs = {m: oracle.State(sc.params.copy(precision="fp64", model=m), sc.x, sc.v, sc.w, sc.r).run(ksteps)
+            for m in ("practical", "simple")}
+    t_oracle = time.perf_counter() - t0
+    out = {"workload": f"box settling: {sc.n:,} spheres r~U[0.8,1.2] mm, RSA loose fill (phi 0.35) in 160x160x400 "
+                       f"mean radii, practical and simple models, skin {skin * 1e3:.3f} mm",
+           "n_particles": sc.n, "steps": args.config2_steps, "oracle_check_steps": ksteps,
+           "oracle_check_s": round(t_oracle, 1), "modes": {}}
+    for name, p in modes.items():
+        model = p.model
+        ref = refs[model]
+        with dem.Simulation(p, sc.x, sc.v, sc.w, sc.r, device=dev_index, cuda_stream=stream.cuda_stream,
+                            max_contacts=args.max_contacts) as s:
+            s.step(ksteps)
+            x, _, _ = s.state()
+            err = float(np.max(np.abs(x - ref.x)))
+            disp = float(np.max(np.linalg.norm(ref.x - sc.x, axis=1)))
+            s.step(20)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(args.config2_steps)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.config2_steps
+        out["modes"][name] = {"value": round(sc.n / (ms / 1e3), 1), "ms_per_step": round(ms, 4),
+                              "max_abs_dx_vs_oracle_m": err, "oracle_max_displacement_m": disp}
+    m = out["modes"]
+    out["fp64_over_fp32_slowdown"] = round(m["fp64_practical"]["ms_per_step"] / m["fp32_practical"]["ms_per_step"], 3)
+    out["practical_over_simple_slowdown_fp32"] = round(
+        m["fp32_practical"]["ms_per_step"] / m["fp32_simple"]["ms_per_step"], 3)
+    return out
 
 
 def run_hopper_bench(args, dem, dev_index, stream, block=0):
@@ -385,9 +451,11 @@ def measured_hbm_gbs():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(list_mode=False):
+    """Hash of the sources of the force kernel (list mode or walk), which the committed
+    ncu summaries record."""
     h = hashlib.sha256()
-    for fn in ("dem_kernels.cu", "dem_dev.cuh"):
+    for fn in ("dem_list.cu" if list_mode else "dem_kernels.cu", "dem_policy.cuh", "dem_dev.cuh"):
         with open(os.path.join(ROOT, "paper_1301_1714_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -410,7 +478,7 @@ def profiled_traffic_per_particle(list_mode=False):
                 bpp = float(line.split(":", 1)[1].strip())
             except ValueError:
                 bpp = None
-    return bpp if (src == kernel_source_hash() and bpp) else None
+    return bpp if (src == kernel_source_hash(list_mode) and bpp) else None
 
 
 # ------------------------------------------------------------------ oracle sample
@@ -440,14 +508,70 @@ def oracle_sample(args, sc, target_s, max_steps=None, state="the same seeded wor
     return value, desc, steps, dt
 
 
+def _oracle_slab_worker(payload):
+    """One process of the all-cores baseline: the oracle on its own slab, timed alone."""
+    import oracle
+    params, x, v, w, r, steps = payload
+    st = oracle.State(params, x, v, w, r)
+    t0 = time.perf_counter()
+    st.run(steps)
+    return len(r), steps, time.perf_counter() - t0
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def oracle_all_cores(args, sc, target_s, procs, state):
+    """The FP64 oracle as it stands, one process per host core, each on its own slab of the
+    workload (disjoint ranges of x; the oracle's arithmetic is untouched), all started
+    together; throughput = every process's particle-steps over the slowest one's time.
+    The pool uses the spawn start method, so no process inherits the parent's CUDA state."""
+    import multiprocessing as mp
+    import oracle
+    order = np.argsort(sc.x[:, 0], kind="stable")
+    n_cal = min(sc.n, 20000)
+    sel = np.sort(order[:n_cal])
+    p64 = sc.params.copy(precision="fp64")
+    t0 = time.perf_counter()
+    oracle.State(p64, sc.x[sel], sc.v[sel], sc.w[sel], sc.r[sel]).run(1)
+    per = (time.perf_counter() - t0) / n_cal
+    steps = 3
+    n_w = int(min(sc.n // procs, max(1000, target_s / (per * steps))))
+    payloads = []
+    for k in range(procs):
+        ids = np.sort(order[k * n_w:(k + 1) * n_w])
+        payloads.append((p64, sc.x[ids], sc.v[ids], sc.w[ids], sc.r[ids], steps))
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_oracle_slab_worker, payloads)
+    dt = max(r_[2] for r_ in res)
+    value = sum(r_[0] * r_[1] for r_ in res) / dt
+    desc = (f"FP64 oracle (C), {procs} processes at once, each {steps} step(s) of its own slab of {n_w:,} spheres "
+            f"(consecutive ranges of x) of {state}; slowest process {dt:.1f} s")
+    return value, desc
+
+
 # ------------------------------------------------------------------ our arm
 def run_ours(args):
     import torch
     from paper_1301_1714_gb300 import dem, replicas
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local_rank = replicas.rank_env()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -494,6 +618,23 @@ def run_ours(args):
         dem.dem_set_particles(h, xs0, vs0, ws0, sc.r)
         t_prep = time.perf_counter() - t_prep
         dem.dem_step(h, max(3, args.warmup))
+        # ---------------- amortization window: the steps per sort and the rate with the
+        # sorts at their natural frequency (the timed window below may be too short to
+        # hold one)
+        amort = None
+        if args.amortize_steps > 0:
+            torch.cuda.synchronize(dev)
+            dem.dem_set_timing(h, True)
+            a_sorts0 = dem.dem_get_diagnostics(h)[14]
+            dem.dem_step(h, args.amortize_steps)
+            aph = dem.dem_get_phase_times(h)
+            a_sorts = dem.dem_get_diagnostics(h)[14] - a_sorts0
+            dem.dem_set_timing(h, False)
+            a_ms = (aph[0] + aph[1]) / max(aph[2], 1)
+            amort = {"steps": args.amortize_steps, "sorts": int(a_sorts),
+                     "steps_per_sort": (round(args.amortize_steps / a_sorts, 1) if a_sorts else None),
+                     "ms_per_step": round(a_ms, 4), "force_ms": round(aph[0] / max(aph[2], 1), 4),
+                     "sort_tail_ms_per_step": round(aph[1] / max(aph[3], 1), 4)}
         # ---------------- timed region (device events on the library's stream)
         if dist:
             dist.barrier()
@@ -543,9 +684,22 @@ def run_ours(args):
         Z = 2.0 * diag["pair_contacts"] / N
         W = diag["wall_contacts"] / N
         b_force = 104.0 + 20.0 * Z + 40.0 * W
+        # the step: the force pass plus the sort's share, (16 c + 16 P + 104) / K bytes per
+        # particle (c cells per particle, P = 3 key passes, K steps per sort)
+        _, _, gdims = dem.dem_get_grid(h)
+        c_cells = float(np.prod(gdims)) / N
+        if amort is not None:
+            K = (amort["steps"] / amort["sorts"]) if amort["sorts"] else float(amort["steps"])
+            b_step = b_force + (16.0 * c_cells + 16.0 * 3 + 104.0) / K
+            amort["value"] = round(replicas.reduce_sum(float(N), dev) / (amort["ms_per_step"] / 1e3), 1)
+            amort["algorithmic_bytes_per_particle"] = round(b_step, 1)
+            amort["cells_per_particle"] = round(c_cells, 3)
+            amort["achieved_gbs"] = round(b_step * N / (amort["ms_per_step"] / 1e3) / 1e9, 1)
         force_ms = phase[0] / max(phase[2], 1)
         sort_ms = phase[1] / max(phase[3], 1)
         peak, peak_src = measured_hbm_gbs()
+        if amort is not None:
+            amort["frac"] = round(amort["achieved_gbs"] / peak, 4)
         achieved = b_force * N / (force_ms / 1e3) / 1e9
         bpp = profiled_traffic_per_particle(p.resort_interval != 1)
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -647,6 +801,8 @@ def run_ours(args):
         serving = run_serve_bench(args, dem, dev.index, stream) if args.serve_requests > 0 else None
         hopper = (run_hopper_bench(args, dem, dev.index, stream, block)
                   if args.hopper_steps > 0 and rank == 0 and world == 1 else None)
+        config2 = (run_config2(args, dem, dev.index, stream)
+                   if args.config2_steps > 0 and rank == 0 and world == 1 else None)
         out = {"metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                "warmup": max(3, args.warmup), "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -656,9 +812,11 @@ def run_ours(args):
                           "sorts_in_timed_steps": int(sorts_timed),
                           "l2": "inputs larger than L2 (no flush needed)",
                           "device_bytes": dem.dem_device_bytes(h), "parallelism": f"replicas x{world}"},
-               "roofline": roof, "gpu_launches": int(launches), "clocks": clocks, "graph_replay": graph,
+               "roofline": roof, "amortized": amort, "gpu_launches": int(launches), "clocks": clocks,
+               "graph_replay": graph,
                "simple": simple, "e2e": e2e,
-               "batch": batch, "serving": serving, "hopper": hopper, "autotune": tuned, "sort_every_step": every,
+               "batch": batch, "serving": serving, "hopper": hopper, "config2": config2, "autotune": tuned,
+               "sort_every_step": every,
                "slabs": slabs,
                "diagnostics": dict({k: diag[k] for k in ("pair_contacts", "wall_contacts", "max_overlap", "ke_trans")},
                                    max_contacts_seen=max_seen, max_contacts=cfg.max_contacts or 32)}
@@ -666,8 +824,17 @@ def run_ours(args):
         dem.dem_destroy(h)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, desc, steps, dt = oracle_sample(args, sc, args.cpu_seconds)
-        out["cpu_baseline"] = {"value": round(v, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        state = "the same seeded workload before settling"
+        v1, desc1, steps, dt = oracle_sample(args, sc, args.cpu_seconds, state=state)
+        single = {"value": round(v1, 1), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc1}
+        nproc = os.cpu_count() or 1
+        procs = nproc if args.cpu_procs == 0 else args.cpu_procs
+        if procs > 1:
+            va, desca = oracle_all_cores(args, sc, args.cpu_seconds, procs, state)
+            out["cpu_baseline"] = {"value": round(va, 1), "unit": UNIT, "cores": procs, "kind": "oracle",
+                                   "sample": desca, "nproc": nproc, "cpu_model": cpu_model(), "single_core": single}
+        else:
+            out["cpu_baseline"] = dict(single, nproc=nproc, cpu_model=cpu_model())
     elif rank == 0:
         out["cpu_baseline"] = None
     if dist:
@@ -713,6 +880,10 @@ def run_reference(args):
 
 def main():
     args = parse()
+    from paper_1301_1714_gb300 import replicas
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one rank per GPU, launched here when the caller did not use torchrun
+        sys.exit(replicas.launch_ranks(args.gpus, [os.path.abspath(__file__), *sys.argv[1:]]))
     if args.impl == "reference":
         run_reference(args)
     else:

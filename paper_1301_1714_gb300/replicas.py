@@ -10,6 +10,10 @@ particle count.
 """
 from __future__ import annotations
 
+import os
+import socket
+import subprocess
+import sys
 from typing import List, Sequence
 
 
@@ -58,3 +62,30 @@ def reduce_sum(value: float, device="cpu") -> float:
     t = _tensor(value, device)
     dist.all_reduce(t)
     return float(t.item())
+
+
+def rank_env():
+    """(world size, rank, local rank) of this process, from the variables torchrun sets;
+    (1, 0, 0) when it runs alone."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def free_port() -> int:
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def launch_ranks(nproc: int, argv: Sequence[str], port: int = 0, timeout: float = None) -> int:
+    """Run `python argv...` as `nproc` ranks on this node through torch.distributed.run
+    (rendezvous on 127.0.0.1): each rank finds WORLD_SIZE, RANK and LOCAL_RANK in its
+    environment (see rank_env). Returns the launcher's exit status (non-zero if any rank
+    failed)."""
+    if nproc < 1:
+        raise ValueError("nproc must be >= 1")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes", "1", "--nproc-per-node", str(nproc),
+           "--master-addr", "127.0.0.1", "--master-port", str(port or free_port()), *argv]
+    return subprocess.run(cmd, timeout=timeout).returncode

@@ -64,3 +64,17 @@ def test_two_gloo_ranks_agree_on_shards_and_reductions():
         assert gathered[rank] == mine
         assert sorted(k for s in gathered for k in s) == list(range(len(fp)))
     assert res[0][4] == res[1][4]
+
+
+def test_launcher_starts_ranks_with_their_bookkeeping(tmp_path):
+    """bench.py --gpus N without torchrun launches N ranks through replicas.launch_ranks:
+    every rank sees world N, its own rank, and the reductions the benchmark uses."""
+    probe = os.path.join(os.path.dirname(os.path.abspath(__file__)), "rank_probe.py")
+    rc = replicas.launch_ranks(2, [probe, str(tmp_path)], timeout=300)
+    assert rc == 0
+    import json
+    got = sorted((json.load(open(tmp_path / f"rank{k}.json")) for k in range(2)), key=lambda d: d["rank"])
+    assert [d["rank"] for d in got] == [0, 1]
+    assert all(d["world"] == 2 and d["group_size"] == 2 for d in got)
+    assert [d["local_rank"] for d in got] == [0, 1]
+    assert all(d["n_total"] == 3000.0 and d["t_max"] == 1.5 for d in got)
