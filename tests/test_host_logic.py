@@ -61,8 +61,8 @@ def test_latency_stats():
 def test_bench_reads_profiled_traffic_only_for_the_profiled_kernel(tmp_path, monkeypatch):
     sys.path.insert(0, ROOT)
     import bench
-    h = bench.kernel_source_hash()
-    assert len(h) == 16
+    h = bench.kernel_source_hash(True)
+    assert len(h) == 16 and h != bench.kernel_source_hash(False)
     prof = tmp_path / "profiles"
     prof.mkdir()
     (prof / "force_kernel_list_drum.md").write_text(f"kernel_source_sha256_16: {h}\ndram_bytes_per_particle: 123.5\n")
