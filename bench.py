@@ -85,11 +85,13 @@ def parse():
     ap.add_argument("--batch-scenes", type=int, default=256, help="scenes of the batched run (0 = skip)")
     ap.add_argument("--batch-steps", type=int, default=300)
     ap.add_argument("--batch-seq-scenes", type=int, default=32, help="scenes timed one by one for comparison")
-    ap.add_argument("--serve-requests", type=int, default=24, help="requests of the serving run (0 = skip)")
-    ap.add_argument("--serve-rate", type=float, default=20.0)
-    ap.add_argument("--serve-nmax", type=int, default=131072)
-    ap.add_argument("--serve-steps", type=str, default="500,2000", help="step budget range of the requests")
-    ap.add_argument("--serve-hbm-gb", type=float, default=16.0)
+    ap.add_argument("--serve-requests", type=int, default=32, help="requests of each serving run (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=20.0, help="arrival rate of the saturated run [1/s]")
+    ap.add_argument("--serve-nmax", type=int, default=1048576)
+    ap.add_argument("--serve-steps", type=str, default="1000,20000", help="step budget range of the requests")
+    ap.add_argument("--serve-hbm-gb", type=float, default=64.0)
+    ap.add_argument("--serve-load", type=float, default=0.7,
+                    help="offered load of the second run, as a fraction of the first run's measured rate (0 = skip)")
     ap.add_argument("--slabs", type=str, default="2,4",
                     help="slab counts of the decomposed runs (sub-domains with halo exchange, sort every step; "
                          "'' = skip)")
@@ -151,17 +153,21 @@ def settle_bed(dem, sc, dev_index, stream, steps, relax):
 
 def run_batch_bench(args, dem, dev_index, stream, block=0):
     """256 independent box-settling scenes (log-uniform 1,024-65,536 spheres, mu ~
-    U[0.1, 0.6], e ~ U[0.5, 0.95]) advanced together in one batch, against the first
-    scenes advanced one by one through their own handles."""
+    U[0.1, 0.6], e ~ U[0.5, 0.95]) advanced together in one batch, with the block size and
+    sort policy the autotuner picks for the batch, against the first scenes advanced one by
+    one through their own handles with the same policy."""
     import torch
-    from paper_1301_1714_gb300 import scenes
+    from paper_1301_1714_gb300 import autotune, scenes
     mix = scenes.batch_mix(seed=args.seed, count=args.batch_scenes, precision="fp32")
     total = sum(sc.n for sc in mix)
-    b = dem.dem_batch_create(precision="fp32", max_contacts=args.max_contacts, block_size=block, device=dev_index,
-                             cuda_stream=stream.cuda_stream)
+    best, table = autotune.tune_batch(mix, device=dev_index, cuda_stream=stream.cuda_stream,
+                                      max_contacts=args.max_contacts)
+    params = [autotune.apply(sc.params, float(sc.r.max()), best) for sc in mix]
+    b = dem.dem_batch_create(precision="fp32", max_contacts=args.max_contacts, block_size=best.block,
+                             device=dev_index, cuda_stream=stream.cuda_stream)
     try:
-        for sc in mix:
-            dem.dem_batch_add(b, sc.params, sc.x, sc.v, sc.w, sc.r, args.batch_steps + 3)
+        for sc, p in zip(mix, params):
+            dem.dem_batch_add(b, p, sc.x, sc.v, sc.w, sc.r, args.batch_steps + 3)
         dem.dem_batch_run(b, 3)                      # pack, first sort, graph capture
         torch.cuda.synchronize()
         l0 = dem.dem_batch_launch_count(b)
@@ -172,11 +178,11 @@ def run_batch_bench(args, dem, dev_index, stream, block=0):
     finally:
         dem.dem_batch_destroy(b)
     seq_n, seq_t = 0, 0.0
-    for sc in mix[:args.batch_seq_scenes]:
-        h = dem.dem_create(dem.config_from_params(sc.params, block_size=block, max_contacts=args.max_contacts),
+    for sc, p in list(zip(mix, params))[:args.batch_seq_scenes]:
+        h = dem.dem_create(dem.config_from_params(p, block_size=best.block, max_contacts=args.max_contacts),
                            dev_index, stream.cuda_stream)
         try:
-            dem.dem_set_walls(h, sc.params.walls)
+            dem.dem_set_walls(h, p.walls)
             dem.dem_set_particles(h, sc.x, sc.v, sc.w, sc.r)
             dem.dem_step(h, 3)
             torch.cuda.synchronize()
@@ -190,9 +196,12 @@ def run_batch_bench(args, dem, dev_index, stream, block=0):
     seq = seq_n * args.batch_steps / seq_t if seq_t > 0 else None
     return {"scenes": len(mix), "particles": total, "steps": args.batch_steps, "value": round(batched, 1),
             "unit": UNIT, "ms_per_step": round(tb * 1e3 / args.batch_steps, 4), "gpu_launches": int(launches),
+            "autotune": {"choice": {"block": best.block, "resort_interval": best.resort,
+                                    "skin_frac_rmax": best.skin_frac},
+                         "table": [[c.block, c.resort, c.skin_frac, round(c.ms_per_step, 4)] for c in table]},
             "sequential_value": round(seq, 1) if seq else None,
-            "sequential_sample": f"first {min(args.batch_seq_scenes, len(mix))} scenes, one handle each, "
-                                 f"{args.batch_steps} steps",
+            "sequential_sample": f"first {min(args.batch_seq_scenes, len(mix))} scenes, one handle each with the "
+                                 f"batch's policy, {args.batch_steps} steps",
             "batched_over_sequential": round(batched / seq, 2) if seq else None}
 
 
@@ -354,20 +363,40 @@ def run_slab_bench(args, dem, dev_index, stream, sc, xs, vs, ws, every):
 
 
 def run_serve_bench(args, dem, dev_index, stream):
-    """Poisson request stream served by continuous batching; completion latency."""
+    """Continuous batching of a Poisson request stream: sizes log-uniform in [1,024,
+    serve_nmax], step budgets uniform in serve_steps, box settling and drum scenes
+    alternating, every request run in list mode (skin 0.1 r_max) and admitted by its
+    device-memory footprint. A fixed count of requests arrives at serve_rate (more work
+    than the GPU can do, so the queue grows); then the same count again at serve_load
+    times the rate the first run achieved (steady state). Latency = completion - arrival."""
     from paper_1301_1714_gb300 import serve
     smin, smax = (int(t) for t in args.serve_steps.split(","))
-    reqs = serve.poisson_requests(args.seed, args.serve_requests, args.serve_rate, 1024, args.serve_nmax, smin, smax)
-    offered = sum(r.scene.n * r.steps for r in reqs) / max(reqs[-1].arrival, 1e-9)
-    with serve.Server(int(args.serve_hbm_gb * 2 ** 30), cuda_stream=stream.cuda_stream, device=dev_index) as srv:
-        wall = srv.run(reqs)
-        stats = serve.latency_stats(srv.finished)
-        work = srv.particle_steps
-    return {"requests": len(reqs), "rate_per_s": args.serve_rate, "n_range": [1024, args.serve_nmax],
-            "step_range": [smin, smax], "hbm_budget_gb": args.serve_hbm_gb, "p50_s": round(stats["p50_s"], 3),
-            "p99_s": round(stats["p99_s"], 3), "value": round(work / wall, 1), "unit": UNIT,
-            "offered": round(offered, 1), "achieved_over_offered": round(work / wall / offered, 3),
-            "wall_s": round(wall, 2)}
+
+    def one_run(rate, seed):
+        reqs = serve.poisson_requests(seed, args.serve_requests, rate, 1024, args.serve_nmax, smin, smax)
+        work = sum(r.scene.n * r.steps for r in reqs)
+        offered = work / max(reqs[-1].arrival, 1e-9)
+        with serve.Server(int(args.serve_hbm_gb * 2 ** 30), cuda_stream=stream.cuda_stream, device=dev_index,
+                          max_contacts=args.max_contacts, skin_frac=0.1) as srv:
+            wall = srv.run(reqs)
+            stats = serve.latency_stats(srv.finished)
+            done = srv.particle_steps
+        return {"requests": len(reqs), "rate_per_s": round(rate, 3), "p50_s": round(stats["p50_s"], 3),
+                "p99_s": round(stats["p99_s"], 3), "mean_s": round(stats["mean_s"], 3),
+                "value": round(done / wall, 1), "unit": UNIT, "offered": round(offered, 1),
+                "achieved_over_offered": round(done / wall / offered, 3), "wall_s": round(wall, 2),
+                "particle_steps": int(done)}
+
+    sat = one_run(args.serve_rate, args.seed)
+    out = {"n_range": [1024, args.serve_nmax], "step_range": [smin, smax], "hbm_budget_gb": args.serve_hbm_gb,
+           "sort_policy": "list mode, skin 0.1 r_max per scene", "saturated": sat}
+    if args.serve_load > 0:
+        mean_work = sat["particle_steps"] / sat["requests"]
+        rate = args.serve_load * sat["value"] / mean_work
+        out["steady"] = dict(one_run(rate, args.seed + 7), load_fraction_of_measured=args.serve_load)
+    # headline fields of the saturated run
+    out.update({k: sat[k] for k in ("p50_s", "p99_s", "value", "unit", "achieved_over_offered")})
+    return out
 
 
 # ------------------------------------------------------------------ clocks

@@ -83,9 +83,13 @@ enum { DEM_TERM_NO_ATTRACTION = 1, DEM_TERM_ROLLING = 2, DEM_TERM_ETA_T = 4, DEM
  *              particle within r_i + r_j + skin is built from the 27 cells and the force
  *              pass reads it instead of walking. K > 1 = as 0, and also at least every K
  *              steps. 0 and K > 1 need skin > 0; they find exactly the same contacts.
- *              In these modes the library stores each window of block_size consecutive
- *              (cell, id) positions ordered by the particles' last contact counts, so
- *              the force kernel's warps get similar amounts of work; results are the same.
+ *              In these modes the library numbers grid cells in bricks of 4 x 4 x 4
+ *              internally and stores each window of block_size consecutive (cell, id)
+ *              positions ordered by the particles' last contact counts, so the force
+ *              kernel's warps get similar amounts of work; a list holds at most 64
+ *              candidates in ascending partner id (a fuller one makes dem_step return
+ *              DEM_ERR_CAPACITY), so a particle's contacts are summed in that order and
+ *              results do not depend on when the sorts happened.
  *  block_size  threads per block of the force kernel (32..256); 0 = automatic (256)
  *  terms       optional force terms added to Eqs. 2-10 (none is in the paper; its force
  *              is built from separable terms so that terms can be added, Sec. 3), an OR of:
@@ -103,8 +107,9 @@ enum { DEM_TERM_NO_ATTRACTION = 1, DEM_TERM_ROLLING = 2, DEM_TERM_ETA_T = 4, DEM
  *  alpha_t     tangential damping factor (DEM_TERM_ETA_T)
  *  k_coh       cohesion energy density [N/m^2] (DEM_TERM_COHESION)
  *  max_contacts  per-particle capacity of the contact/history list (incl. walls);
- *              0 = 32; neighbour lists hold 2 x max_contacts. Exceeding either makes
- *              dem_step return DEM_ERR_CAPACITY.
+ *              0 = 32. Neighbour lists (resort_interval != 1) hold 64 candidates
+ *              whatever max_contacts is. Exceeding either makes dem_step return
+ *              DEM_ERR_CAPACITY; no contact is dropped silently.
  */
 typedef struct {
     int32_t model;
@@ -238,7 +243,12 @@ dem_status dem_get_phase_times(const dem_handle* h, double* out4);
  * Sec. 4.2) covers all of them; each particle reads its own scene's parameters, grid and
  * walls. Scenes differ in size, dt, mu, alpha, walls and grid, but share precision,
  * model and stiffness law. A scene's result does not depend on the other scenes in the
- * batch. Scenes sort every step (resort_interval must be 1). */
+ * batch. The first scene added sets the batch's sort policy (its resort_interval): either
+ * every scene sorts every step (1), or every scene keeps neighbour lists with its own skin
+ * and the whole batch sorts when a particle of any scene has moved half its scene's skin
+ * (0), or also every K steps (K > 1); later scenes must have the same resort_interval.
+ * In list mode a scene's results are still those of its own run, bit for bit, because
+ * they do not depend on when sorts happen. */
 typedef struct dem_batch dem_batch;
 
 /* Creates an empty batch on `device` / `cuda_stream` (a non-legacy stream lets the step

@@ -69,3 +69,41 @@ def tune(params, x, v, w, r, candidates: Sequence[Tuple[int, int, float]] = DEFA
         raise RuntimeError("no autotune candidate ran (contact capacity too small for every one)")
     best = min(table, key=lambda t: t.ms_per_step)
     return best, table
+
+
+# candidates for a batch of many small scenes: the whole batch sorts when any particle of
+# any scene has moved half its skin, so larger skins pay off sooner than for one scene
+BATCH_CANDIDATES: Tuple[Tuple[int, int, float], ...] = (
+    (256, 1, 0.0), (128, 0, 0.1), (256, 0, 0.1), (128, 0, 0.2), (128, 0, 0.3),
+)
+
+
+def tune_batch(mix, precision: str = "fp32", candidates: Sequence[Tuple[int, int, float]] = BATCH_CANDIDATES,
+               steps: int = 60, warmup: int = 20, device: int = 0, cuda_stream=None,
+               max_contacts: int = 0) -> Tuple[Choice, List[Choice]]:
+    """The block size and sort policy for a batch of scenes (each scene's skin is the
+    fraction of its own largest radius), by timing short runs of the whole batch."""
+    import time
+    table: List[Choice] = []
+    for block, resort, sk in candidates:
+        c = Choice(block, resort, sk, 0.0, 0.0, 0.0)
+        b = dem.dem_batch_create(precision=precision, max_contacts=max_contacts, block_size=block, device=device,
+                                 cuda_stream=cuda_stream)
+        try:
+            for sc in mix:
+                p = apply(sc.params, float(max(sc.r)), c)
+                dem.dem_batch_add(b, p, sc.x, sc.v, sc.w, sc.r, warmup + steps + 1)
+            dem.dem_batch_run(b, warmup)
+            t0 = time.perf_counter()
+            dem.dem_batch_run(b, steps)
+            c.ms_per_step = (time.perf_counter() - t0) * 1e3 / steps
+        except dem.DemError as e:
+            if e.status != dem.DEM_ERR_CAPACITY:
+                raise
+            continue
+        finally:
+            dem.dem_batch_destroy(b)
+        table.append(c)
+    if not table:
+        raise RuntimeError("no autotune candidate ran for the batch")
+    return min(table, key=lambda t: t.ms_per_step), table

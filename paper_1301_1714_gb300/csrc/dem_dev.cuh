@@ -54,7 +54,9 @@ struct SceneDev {
     int32_t terms;              // optional force terms (DEM_TERM_*)
     int32_t bshift;             // cell order: 0 row-major; s > 0 bricks of (2^s)^3 cells (list mode)
     int32_t bdims[3];           // bricks per axis (bshift > 0)
-    int32_t pad4;
+    float skin_f;               // list mode: Verlet skin [m] of the scene's neighbour lists
+    float thresh2_f;            // list mode: squared displacement since the last sort that forces a sort
+    float pad4;
     double mu_roll;             // rolling resistance coefficient
     double alpha_t;             // tangential damping factor
     double kcoh_pi;             // pi * cohesion energy density

@@ -50,8 +50,6 @@ struct Domain {
     int list_mode = 0;
     int maxn = DEM_LIST_CAP;
     int interval = 1;              // sort at least every `interval` steps (0 = skin only)
-    float skin_f = 0.f;            // skin [m]
-    float thresh2 = 0.f;           // squared displacement that forces a sort
     uint32_t* ncnt = nullptr;
     uint32_t* nl = nullptr;
     float4* ref = nullptr;         // positions at the last sort

@@ -229,6 +229,12 @@ void fill_scene(dem_handle* h, SceneDev& S, uint32_t p0, uint32_t np, uint32_t c
         X = std::max(X, std::max(std::fabs(c.domain_lo[a]), std::fabs(c.domain_hi[a])) + ext);
     }
     S.eps_f = (float)(std::ldexp(1.0, -20) * (X + 2.0 * h->rmax));
+    if (c.resort_interval != 1) {
+        // a particle that moved skin/2 less the FP32 position margin forces a sort
+        const double t = std::max(0.5 * c.skin - (double)S.eps_f, 0.0);
+        S.skin_f = (float)c.skin;
+        S.thresh2_f = (float)(t * t);
+    }
     for (size_t k = 0; k < h->walls.size(); ++k) S.walls[k] = make_wall(h->walls[k]);
 }
 
@@ -484,13 +490,6 @@ dem_status load_particles(dem_handle* h, int64_t n64, const double* x, const dou
     *d.ctrl_host = CtrlDev{};
     d.ctrl_host->rebuild = 1;
     CK(h, cudaMemcpyAsync(d.ctrl, d.ctrl_host, sizeof(CtrlDev), cudaMemcpyHostToDevice, d.stream));
-    if (d.list_mode) {
-        // a particle that moved skin/2 less the FP32 position margin forces a sort
-        const double margin = (double)d.h_scenes[0].eps_f;
-        const double t = std::max(0.5 * c.skin - margin, 0.0);
-        d.thresh2 = (float)(t * t);
-        d.skin_f = (float)c.skin;
-    }
     d.h_cur = 0;
     if (n > 0) {
         CK(h, cudaMemsetAsync(d.hcnt[0], 0, (size_t)n * 4, d.stream));
@@ -1270,6 +1269,7 @@ struct dem_batch {
     size_t stage_cap = 0;
     uint32_t* d_map = nullptr;
     size_t map_cap = 0;
+    int resort_interval = -1;   // sort policy of every scene (set by the first scene added)
 };
 
 namespace {
@@ -1350,8 +1350,8 @@ dem_status repack(dem_batch* b) {
     nd.block = od.block;
     nd.sort_blocks = od.sort_blocks;
     nd.stream = od.stream;
-    nd.list_mode = 0;
-    nd.interval = 1;
+    nd.list_mode = (b->resort_interval >= 0 && b->resort_interval != 1) ? 1 : 0;
+    nd.interval = b->resort_interval < 0 ? 1 : b->resort_interval;
     nd.st = od.st;
     nd.st_host = od.st_host;
     nd.ctrl = od.ctrl;
@@ -1506,7 +1506,11 @@ dem_status dem_batch_add(dem_batch* b, const dem_config* cfg, int nwalls, const 
     if (validate_config(cfg, why) != DEM_OK) return bfail(b, DEM_ERR_INVALID_ARG, why);
     if (cfg->precision != b->d.precision || cfg->model != b->d.model || cfg->stiffness != b->d.stiffness)
         return bfail(b, DEM_ERR_INVALID_ARG, "precision, model and stiffness must match the batch");
-    if (cfg->resort_interval != 1) return bfail(b, DEM_ERR_INVALID_ARG, "batches sort every step (resort_interval 1)");
+    // the batch's sort policy is its first scene's: every scene sorts every step, or every
+    // scene keeps neighbour lists (each with its own skin) under one resort_interval
+    if (b->resort_interval < 0) b->resort_interval = cfg->resort_interval;
+    if (cfg->resort_interval != b->resort_interval)
+        return bfail(b, DEM_ERR_INVALID_ARG, "every scene of a batch must have the batch's resort_interval");
     if (nwalls < 0 || nwalls > DEM_MAX_WALLS || (nwalls > 0 && !walls)) return bfail(b, DEM_ERR_INVALID_ARG, "nwalls");
     if (n < 0 || n > 0x7FFFFF00 || step_budget < 0) return bfail(b, DEM_ERR_INVALID_ARG, "n or step_budget");
     if (n > 0 && (!x || !v || !w || !r)) return bfail(b, DEM_ERR_INVALID_ARG, "x, v, w and r are required");
@@ -1671,8 +1675,10 @@ int64_t dem_batch_device_bytes(const dem_batch* b) {
     const size_t N = d.cap, M = d.maxc, C = (size_t)d.cells_cap + 1;
     const size_t T = d.precision == 0 ? 8 : 4;
     const size_t state = d.precision == 0 ? N * (9 * 8 + 8) : N * (4 * 16 + 4);
-    return (int64_t)(2 * state + 2 * (N * 4 + N * 4 * M + N * T * 3 * M) + 5 * N * 4 + 2 * C * 4 +
-                     b->stage_cap * 76 + b->map_cap * 4);
+    size_t bytes = 2 * state + 2 * (N * 4 + N * 4 * M + N * T * 3 * M) + 5 * N * 4 + 2 * C * 4 +
+                   b->stage_cap * 76 + b->map_cap * 4;
+    if (d.list_mode) bytes += N * (4 + 4 * (size_t)DEM_LIST_CAP + 16 + 8);
+    return (int64_t)bytes;
 }
 
 int64_t dem_batch_launch_count(const dem_batch* b) { return b ? b->d.launches : 0; }

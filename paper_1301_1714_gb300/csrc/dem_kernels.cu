@@ -437,24 +437,29 @@ __global__ void k_rank_cell(uint32_t n, typename PR::State S0, typename PR::Stat
     }
 }
 
-// One block per window of blockDim.x (cell, id) positions: fin[q] = final position.
-__global__ void __launch_bounds__(256) k_window(uint32_t n, const CtrlDev* ctrl, const uint32_t* __restrict__ wkey,
-                                                uint32_t* __restrict__ fin) {
+// One block per window of blockDim.x (cell, id) positions: fin[q] = final position. A
+// window is split where one scene ends and the next begins (scenes are contiguous in the
+// (cell, id) order), so every particle stays inside its scene's range of positions.
+__global__ void __launch_bounds__(256) k_window(uint32_t n, const SceneDev* scenes, int nscenes, const CtrlDev* ctrl,
+                                                const uint32_t* __restrict__ wkey, uint32_t* __restrict__ fin) {
     if (!ctrl->rebuild) return;
     __shared__ uint32_t s_key[256];
+    __shared__ int32_t s_sc[256];
     const uint32_t w = blockDim.x;
     for (uint32_t base = blockIdx.x * w; base < n; base += gridDim.x * w) {
         const uint32_t q = base + threadIdx.x;
         const uint32_t key = q < n ? min(wkey[q], 0xFFFFu) : 0u;
+        const int sc = q < n ? scene_of(scenes, nscenes, q) : -1;
         __syncthreads();
         s_key[threadIdx.x] = key;
+        s_sc[threadIdx.x] = sc;
         __syncthreads();
         uint32_t rank = 0;
         for (uint32_t t = 0; t < w; ++t) {
             const uint32_t kt = s_key[t];
-            rank += (kt > key || (kt == key && t < threadIdx.x)) ? 1u : 0u;
+            rank += (s_sc[t] == sc && (kt > key || (kt == key && t < threadIdx.x))) ? 1u : 0u;
         }
-        if (q < n) fin[q] = base + rank;
+        if (q < n) fin[q] = max(base, scenes[sc].p0) + rank;
     }
 }
 
@@ -765,7 +770,7 @@ cudaError_t run_rebuild(Domain& d) {
             k_rank_cell<PF32><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.S32[0], d.S32[1], d.ctrl, d.key, d.cs,
                                                                      d.tmp, hc, d.canon, d.rank);
         DEM_LAUNCH_CHECK();
-        k_window<<<wg, wb, 0, d.stream>>>(d.n, d.ctrl, d.rank, d.fin);
+        k_window<<<wg, wb, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.ctrl, d.rank, d.fin);
         DEM_LAUNCH_CHECK();
         if (d.precision == 0)
             k_gather<PF64><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.S64[0], d.S64[1], d.ctrl, d.key, d.canon,

@@ -12,8 +12,8 @@
 // Every particle evaluates all of its contacts (each pair twice, once from each side, with
 // arithmetic that makes the two results exact negatives), so a step is one pass with no
 // exchange between particles; springs are stored per particle, keyed by partner id. No
-// floating-point atomics: a particle's sums run in list order, so results do not depend
-// on the block size.
+// floating-point atomics: a particle's sums run in list order (ascending partner id), so
+// results depend neither on the block size nor on when the sorts happened.
 #include <algorithm>
 
 #include <cuda_runtime.h>
@@ -42,7 +42,6 @@ struct ListArgs {
     const uint32_t* ncnt;        // list lengths
     const uint32_t* nl;          // list entries (stored index), slot-major
     const float4* ref;           // positions at the last sort
-    float thresh2;               // squared displacement that forces a sort
     int interval;                // sort at least every `interval` steps (0: never forced)
     const uint32_t* perm;
     const uint32_t* hin_cnt;     // springs read
@@ -59,24 +58,29 @@ struct ListArgs {
 // ------------------------------------------------------------------ list build
 // Candidates of particle q at a sort: every particle of the 27 cells around q's cell
 // (Eq. 12; list mode numbers the cells brick by brick, so each cell is looked up on its
-// own) within r_i + r_j + skin (+ the FP32 margin). With cells of edge >= 2 r_max + skin
-// no pair that comes into contact before some particle has moved skin/2 is missed. A list
-// longer than DEM_LIST_CAP is reported (the step returns DEM_ERR_CAPACITY).
+// own) within r_i + r_j + skin (+ the FP32 margin), the skin of q's scene. With cells of
+// edge >= 2 r_max + skin no pair that comes into contact before some particle has moved
+// skin/2 is missed. A list is kept in ascending partner id, so the force pass sums a
+// particle's contacts in that order whenever the list was built: results do not depend on
+// when sorts happen (a batch sorts all its scenes together, and each scene still gets the
+// bits of its own run). A list longer than DEM_LIST_CAP is reported (the step returns
+// DEM_ERR_CAPACITY).
 template <class PR>
 __global__ void __launch_bounds__(256) k_nlist(uint32_t n, const SceneDev* scenes, int nscenes, typename PR::State S0,
                                                typename PR::State S1, const CtrlDev* ctrl,
                                                const uint32_t* __restrict__ skey, const uint32_t* __restrict__ cs,
                                                const uint32_t* __restrict__ fin, uint32_t* __restrict__ ncnt,
-                                               uint32_t* __restrict__ nl, size_t cap, float skin, StatusDev* st) {
+                                               uint32_t* __restrict__ nl, size_t cap, StatusDev* st) {
     if (!ctrl->rebuild) return;
     const typename PR::State A = ctrl->cur ? S1 : S0;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         const SceneDev& S = scenes[scene_of(scenes, nscenes, q)];
         const typename PR::Self me = PR::load(A, q);
-        const float extra = skin + S.eps_f;
+        const float extra = S.skin_f + S.eps_f;
         int ix, iy, iz;
         cell_coords(S, skey[q] - S.c0, ix, iy, iz);
         uint32_t m = 0;
+        uint32_t lid[DEM_LIST_CAP], lj[DEM_LIST_CAP];   // the list so far, ascending partner id
         for (int dz = -1; dz <= 1; ++dz)
             for (int dy = -1; dy <= 1; ++dy)
                 for (int dx = -1; dx <= 1; ++dx) {
@@ -87,12 +91,23 @@ __global__ void __launch_bounds__(256) k_nlist(uint32_t n, const SceneDev* scene
                     for (uint32_t jc = __ldg(&cs[c]); jc < c1; ++jc) {
                         const uint32_t j = fin[jc];   // the cell table holds (cell, id) positions
                         if (j == q || !PR::within(A, me, j, extra)) continue;
-                        if (m < DEM_LIST_CAP) nl[(size_t)m * cap + q] = j;
+                        if (m < DEM_LIST_CAP) {
+                            const uint32_t idj = __ldg(&A.id[j]);
+                            uint32_t k = m;
+                            for (; k > 0 && lid[k - 1] > idj; --k) {
+                                lid[k] = lid[k - 1];
+                                lj[k] = lj[k - 1];
+                            }
+                            lid[k] = idj;
+                            lj[k] = j;
+                        }
                         ++m;
                     }
                 }
         if (m > DEM_LIST_CAP) raise_status(st, ST_LIST, (int32_t)q);
-        ncnt[q] = min(m, (uint32_t)DEM_LIST_CAP);
+        m = min(m, (uint32_t)DEM_LIST_CAP);
+        for (uint32_t k = 0; k < m; ++k) nl[(size_t)k * cap + q] = lj[k];
+        ncnt[q] = m;
     }
 }
 
@@ -270,7 +285,7 @@ __global__ void __launch_bounds__(256, DEM_LIST_MIN_BLOCKS) k_list(ListArgs<PR> 
             // this step end with a sort and new lists
             const float4 r0 = __ldg(&a.ref[q]);
             const float ex = pnew.x - r0.x, ey = pnew.y - r0.y, ez = pnew.z - r0.z;
-            if (ex * ex + ey * ey + ez * ez > a.thresh2 || !finite) atomicOr(&a.ctrl->rebuild, 1);
+            if (ex * ex + ey * ey + ez * ez > S.thresh2_f || !finite) atomicOr(&a.ctrl->rebuild, 1);
         }
     }
     // warp-aggregated counters (every lane reaches this point)
@@ -307,10 +322,10 @@ cudaError_t run_lists(Domain& d) {
     if (d.n == 0) return cudaSuccess;
     if (d.precision == 0)
         k_nlist<PF64><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S64[0], d.S64[1], d.ctrl, d.skey,
-                                                          d.cs, d.fin, d.ncnt, d.nl, d.cap, d.skin_f, d.st);
+                                                          d.cs, d.fin, d.ncnt, d.nl, d.cap, d.st);
     else
         k_nlist<PF32><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S32[0], d.S32[1], d.ctrl, d.skey,
-                                                          d.cs, d.fin, d.ncnt, d.nl, d.cap, d.skin_f, d.st);
+                                                          d.cs, d.fin, d.ncnt, d.nl, d.cap, d.st);
     DEM_LAUNCH_CHECK();
     return cudaSuccess;
 }
@@ -332,7 +347,6 @@ static cudaError_t force_list_impl(Domain& d, const typename PR::State& S0, cons
     a.ncnt = d.ncnt;
     a.nl = d.nl;
     a.ref = d.ref;
-    a.thresh2 = d.thresh2;
     a.interval = d.interval;
     a.perm = d.perm;
     const int hi = d.h_cur, ho = 1 - d.h_cur;

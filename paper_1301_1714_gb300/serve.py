@@ -20,11 +20,21 @@ import numpy as np
 
 from . import dem
 
-# device bytes per particle of a batch (two state sets, two spring buffers of 32 slots,
-# sort arrays) and per cell (counts + starts); used for admission
-BYTES_PER_PARTICLE = {"fp32": 2 * 68 + 2 * (4 + 4 * 32 + 4 * 3 * 32) + 20 + 76,
-                      "fp64": 2 * 80 + 2 * (4 + 4 * 32 + 8 * 3 * 32) + 20 + 76}
+# device bytes of a batch, as dem_batch_device_bytes counts them: per particle two state
+# sets, two spring buffers of max_contacts slots, the sort arrays, the staging and map
+# buffers, and (list mode) the neighbour list of 64 entries with its count, reference
+# position and window maps; per cell the counts and the starts
+LIST_CAP = 64
 BYTES_PER_CELL = 8
+
+
+def bytes_per_particle(precision: str = "fp32", max_contacts: int = 32, list_mode: bool = False) -> int:
+    state, t = (68, 4) if precision == "fp32" else (80, 8)
+    m = max_contacts or 32
+    b = 2 * state + 2 * (4 + 4 * m + t * 3 * m) + 20 + 76 + 4
+    if list_mode:
+        b += 4 + 4 * LIST_CAP + 16 + 8
+    return b
 
 
 @dataclass(order=True)
@@ -34,45 +44,71 @@ class Request:
     scene: object = field(compare=False)
     steps: int = field(compare=False)
     slot: int = field(default=-1, compare=False)
+    params: object = field(default=None, compare=False)   # what the server runs it with
     admitted: float = field(default=0.0, compare=False)
     done: float = field(default=0.0, compare=False)
     result: Optional[np.ndarray] = field(default=None, compare=False)
 
 
-def footprint(scene, precision="fp32") -> int:
+def footprint(scene, precision="fp32", max_contacts: int = 32) -> int:
+    """Device bytes the scene adds to a batch (an upper bound of what
+    dem_batch_device_bytes grows by)."""
     p = scene.params
     cells = 1
     for a in range(3):
         cells *= max(1, int(np.ceil((p.domain_hi[a] - p.domain_lo[a]) / p.cell_size)))
-    return BYTES_PER_PARTICLE[precision] * scene.n + BYTES_PER_CELL * cells
+    per = bytes_per_particle(precision, max_contacts, p.resort_interval != 1)
+    return per * scene.n + BYTES_PER_CELL * cells
 
 
 class Server:
+    """skin_frac: None runs every request sorting every step (as submitted); a number runs
+    every request in list mode with a skin of skin_frac times its largest radius (the
+    whole batch sorts when any particle has moved half its scene's skin). max_contacts
+    and block_size are the batch's (dem_batch_create)."""
+
     def __init__(self, hbm_budget: int, precision: str = "fp32", model: str = "practical", chunk: int = 200,
-                 device: int = 0, cuda_stream=None, keep_results: bool = False):
+                 device: int = 0, cuda_stream=None, keep_results: bool = False, max_contacts: int = 0,
+                 block_size: int = 0, skin_frac=None):
         self.budget = int(hbm_budget)
         self.precision = precision
         self.chunk = int(chunk)
         self.keep = keep_results
-        self.b = dem.dem_batch_create(precision=precision, model=model, device=device, cuda_stream=cuda_stream)
+        self.max_contacts = int(max_contacts)
+        self.skin_frac = skin_frac
+        self.b = dem.dem_batch_create(precision=precision, model=model, max_contacts=max_contacts,
+                                      block_size=block_size, device=device, cuda_stream=cuda_stream)
         self.waiting: List[Request] = []      # heap by arrival
         self.resident: Dict[int, Request] = {}
         self.finished: List[Request] = []
         self.used = 0
         self.particle_steps = 0
 
+    def run_params(self, scene):
+        """The parameters the server runs a scene with."""
+        p = scene.params
+        if self.skin_frac is None:
+            return p
+        skin = float(self.skin_frac) * float(np.max(scene.r))
+        return p.copy(resort_interval=0, skin=skin, cell_size=p.cell_size + skin)
+
+    def footprint(self, req: Request) -> int:
+        sc = req.scene
+        return footprint(type(sc)(**dict(sc.__dict__, params=req.params)), self.precision, self.max_contacts or 32)
+
     def submit(self, req: Request):
+        req.params = self.run_params(req.scene)
         heapq.heappush(self.waiting, req)
 
     def _admit(self, now: float):
         while self.waiting and self.waiting[0].arrival <= now:
             req = self.waiting[0]
-            fp = footprint(req.scene, self.precision)
+            fp = self.footprint(req)
             if self.resident and self.used + fp > self.budget:
                 break                                   # wait for memory to free up
             heapq.heappop(self.waiting)
             sc = req.scene
-            req.slot = dem.dem_batch_add(self.b, sc.params, sc.x, sc.v, sc.w, sc.r, req.steps)
+            req.slot = dem.dem_batch_add(self.b, req.params, sc.x, sc.v, sc.w, sc.r, req.steps)
             req.admitted = now
             self.resident[req.slot] = req
             self.used += fp
@@ -91,7 +127,7 @@ class Server:
                 req.result = dem.dem_batch_get_state(self.b, slot, req.scene.n)[0]
             dem.dem_batch_remove(self.b, slot)
             req.done = now
-            self.used -= footprint(req.scene, self.precision)
+            self.used -= self.footprint(req)
             self.particle_steps += req.scene.n * req.steps
             self.finished.append(req)
         return True

@@ -175,3 +175,68 @@ def test_injected_allocation_failure_is_reported_and_recoverable(torch_cuda, mon
         dem.dem_step(h, 5)
     finally:
         dem.dem_destroy(h)
+
+
+def listed(p, skin_frac=0.1):
+    skin = skin_frac * 1e-3
+    return p.copy(resort_interval=0, skin=skin, cell_size=p.cell_size + skin)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_list_mode_batch_scene_equals_alone_and_oracle(torch_cuda, precision):
+    """A batch of scenes in list mode (each with its own skin) sorts all together when any
+    particle has moved half its scene's skin; because a particle's contacts are summed in
+    ascending partner id, each scene still gets the bits of its own run, and follows the
+    oracle (FP64 within 1e-9 m)."""
+    torch = torch_cuda
+    stream = torch.cuda.Stream()
+    mix = [scenes.box_lattice_n(seed=50 + k, n=n, e=e, mu=mu, precision=precision)
+           for k, (n, e, mu) in enumerate([(1024, 0.9, 0.3), (1500, 0.6, 0.5), (2048, 0.95, 0.6)])]
+    mix = [type(sc)(**dict(sc.__dict__, params=listed(sc.params, f))) for sc, f in zip(mix, (0.1, 0.05, 0.2))]
+    budgets = [300, 200, 250]
+    b = dem.dem_batch_create(precision=precision, cuda_stream=stream.cuda_stream)
+    try:
+        slots = [dem.dem_batch_add(b, sc.params, sc.x, sc.v, sc.w, sc.r, bud) for sc, bud in zip(mix, budgets)]
+        done = []
+        for _ in range(10):
+            done += dem.dem_batch_run(b, 1000)
+            if len(done) == len(mix):
+                break
+        assert sorted(done) == sorted(slots)
+        for sc, sl, bud in zip(mix, slots, budgets):
+            xb, vb, wb = dem.dem_batch_get_state(b, sl, sc.n)
+            xa, va, wa = alone(sc, bud)
+            assert np.array_equal(xa, xb) and np.array_equal(va, vb) and np.array_equal(wa, wb)
+            if precision == "fp64":
+                ref = oracle.State(sc.params, sc.x, sc.v, sc.w, sc.r).run(bud)
+                assert np.max(np.abs(xb - ref.x)) <= 1e-9
+    finally:
+        dem.dem_batch_destroy(b)
+
+
+def test_list_mode_batch_scene_joining_mid_run_equals_alone(torch_cuda):
+    torch = torch_cuda
+    stream = torch.cuda.Stream()
+    first = scenes.box_lattice_n(seed=61, n=2000, precision="fp32")
+    late = scenes.box_lattice_n(seed=62, n=1200, e=0.7, mu=0.4, precision="fp32")
+    first = type(first)(**dict(first.__dict__, params=listed(first.params)))
+    late = type(late)(**dict(late.__dict__, params=listed(late.params, 0.15)))
+    b = dem.dem_batch_create(precision="fp32", cuda_stream=stream.cuda_stream)
+    try:
+        s1 = dem.dem_batch_add(b, first.params, first.x, first.v, first.w, first.r, 400)
+        dem.dem_batch_run(b, 150)
+        s2 = dem.dem_batch_add(b, late.params, late.x, late.v, late.w, late.r, 300)
+        done = []
+        for _ in range(10):
+            done += dem.dem_batch_run(b, 500)
+            if len(done) == 2:
+                break
+        for sc, sl, bud in ((first, s1, 400), (late, s2, 300)):
+            xb, _, _ = dem.dem_batch_get_state(b, sl, sc.n)
+            xa, _, _ = alone(sc, bud)
+            assert np.array_equal(xa, xb)
+        # a scene with another sort policy is refused
+        with pytest.raises(dem.DemError):
+            dem.dem_batch_add(b, late.params.copy(resort_interval=1, skin=0.0), late.x, late.v, late.w, late.r, 10)
+    finally:
+        dem.dem_batch_destroy(b)

@@ -46,7 +46,9 @@ def test_footprint_grows_with_particles_and_cells():
     small = scenes.box_lattice_n(seed=1, n=2000, precision="fp32")
     large = scenes.box_lattice_n(seed=1, n=20000, precision="fp32")
     fs, fl = serve.footprint(small), serve.footprint(large)
-    assert fl > fs > serve.BYTES_PER_PARTICLE["fp32"] * small.n
+    assert fl > fs > serve.bytes_per_particle("fp32") * small.n
+    assert serve.bytes_per_particle("fp32", 24) < serve.bytes_per_particle("fp32", 32)
+    assert serve.bytes_per_particle("fp32", 24, True) > serve.bytes_per_particle("fp32", 24)
     assert serve.footprint(small, "fp64") > fs
 
 
