@@ -303,8 +303,13 @@ void dem_batch_destroy(dem_batch* b);
  * library's device memory, present on every GPU that loads the library until the
  * process exits; n > DEM_STATIC_SORT_MAX_N or more than DEM_STATIC_SORT_MAX_CELLS cells
  * returns DEM_ERR_INVALID_ARG. The first call on a device looks up that array's device
- * address (once per device), so make the first call before any stream capture. All calls
- * share the array: calls whose work overlaps on the GPU race and give wrong results. */
+ * address and keeps it for the life of the process (so make the first call before any
+ * stream capture; a device reset while the library is loaded is not supported). All
+ * calls share the array: calls whose work overlaps on the GPU race and give wrong results.
+ * The place of a particle within its cell is found by comparing it with every cell-mate,
+ * so the time grows with the square of the cells' occupancy: a cell edge near the largest
+ * diameter keeps it to a few particles per cell, while a grid of a single cell holding
+ * the maximum of 262,144 particles takes seconds. */
 dem_status dem_sort_cells_static(int64_t n, const double* x, const double* origin, double cell, const int64_t* dims,
                                  uint32_t* cell_of, uint32_t* order, uint32_t* cell_start, void* cuda_stream);
 

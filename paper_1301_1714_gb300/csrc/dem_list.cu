@@ -28,6 +28,7 @@
 #define DEM_LIST_MIN_BLOCKS 4
 #endif
 
+
 namespace demgb {
 
 template <class PR>
@@ -112,6 +113,7 @@ __global__ void __launch_bounds__(256) k_nlist(uint32_t n, const SceneDev* scene
 }
 
 // ------------------------------------------------------------------- force pass
+
 // MODEL: 0 the practical law, 1 the simple law (Eq. 1), 2 the practical law with the
 // scene's optional terms. EVAL: forces and torques by id instead of the update.
 template <class PR, int MODEL, bool EVAL>

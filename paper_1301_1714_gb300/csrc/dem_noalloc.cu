@@ -146,7 +146,8 @@ __global__ void k_sa_scatter(uint32_t n, const uint32_t* __restrict__ cell_of, c
     if (k < n) scratch[SA_OFF_TMP + cell_start[cell_of[k]] + scratch[SA_OFF_RANK + k]] = k;
 }
 
-// place of particle p in its cell = number of cell-mates with a smaller id
+// place of particle p in its cell = number of cell-mates with a smaller id (each thread
+// reads its whole cell, so the work grows with the square of the cells' occupancy)
 __global__ void k_sa_order(uint32_t n, const uint32_t* __restrict__ cell_of, const uint32_t* __restrict__ cell_start,
                            const uint32_t* scratch, uint32_t* __restrict__ order) {
     const uint32_t s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -166,11 +167,11 @@ extern "C" dem_status dem_sort_cells_static(int64_t n, const double* x, const do
                                             const int64_t* dims, uint32_t* cell_of, uint32_t* order,
                                             uint32_t* cell_start, void* cuda_stream) {
     if (n < 0 || !origin || !dims || !(cell > 0.0)) return DEM_ERR_INVALID_ARG;
-    if (dims[0] < 1 || dims[1] < 1 || dims[2] < 1) return DEM_ERR_INVALID_ARG;
+    // each axis first (so that the product cannot overflow), then the product
+    for (int a = 0; a < 3; ++a)
+        if (dims[a] < 1 || dims[a] > (int64_t)SA_MAX_CELLS) return DEM_ERR_INVALID_ARG;
     const int64_t ncells = dims[0] * dims[1] * dims[2];
-    if (n > (int64_t)SA_MAX_N || ncells > (int64_t)SA_MAX_CELLS || dims[0] > SA_MAX_CELLS || dims[1] > SA_MAX_CELLS ||
-        dims[2] > SA_MAX_CELLS)
-        return DEM_ERR_INVALID_ARG;
+    if (n > (int64_t)SA_MAX_N || ncells > (int64_t)SA_MAX_CELLS) return DEM_ERR_INVALID_ARG;
     if (!cell_start || (n > 0 && (!x || !cell_of || !order))) return DEM_ERR_INVALID_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= SA_MAX_DEVICES) {

@@ -90,3 +90,44 @@ def test_static_sort_rejects_sizes_beyond_its_maximum(torch_cuda):
     o1 = torch.empty(1, dtype=torch.int32, device="cuda")
     with pytest.raises(dem.DemError):
         dem.dem_sort_cells_static(x1, (0, 0, 0), 1.0, (1025, 1024, 1), o1, o1, cs)
+
+
+def test_static_sort_at_its_maximum_sizes_matches_the_oracle(torch_cuda):
+    """262,144 particles on a grid of 128 x 128 x 64 = 1,048,576 cells (both maxima),
+    against the oracle's cell map, (cell, id) order and cell-start table directly."""
+    import oracle
+    torch = torch_cuda
+    n = dem.STATIC_SORT_MAX_N
+    dims = (128, 128, 64)
+    assert dims[0] * dims[1] * dims[2] == dem.STATIC_SORT_MAX_CELLS
+    cell = 1.0 / 64
+    rng = np.random.default_rng(23)
+    xh = rng.uniform(0.0, 1.0, size=(n, 3)) * np.array(dims) * cell
+    xh[:100] = rng.uniform(-0.5, 2.5, size=(100, 3))          # some outside the grid (clamped)
+    p = scenes.Params(precision="fp64", cell_size=cell, domain_lo=(0.0, 0.0, 0.0),
+                      domain_hi=tuple(d * cell for d in dims))
+    assert oracle.grid_dims(p) == dims
+    key, _ = oracle.cell_keys(p, xh)
+    order, skey = oracle.sort_by_cell(key)
+    start = oracle.cell_start(skey, dims[0] * dims[1] * dims[2])
+    x = torch.tensor(xh, dtype=torch.float64, device="cuda")
+    cell_of = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    gorder = torch.full((n,), -1, dtype=torch.int32, device="cuda")
+    cs = torch.full((dims[0] * dims[1] * dims[2] + 1,), -1, dtype=torch.int32, device="cuda")
+    for _ in range(2):   # twice in a row on the shared array
+        dem.dem_sort_cells_static(x, (0.0, 0.0, 0.0), cell, dims, cell_of, gorder, cs)
+        torch.cuda.synchronize()
+        assert np.array_equal(cell_of.cpu().numpy().view(np.uint32).astype(np.uint64), key)
+        assert np.array_equal(gorder.cpu().numpy().view(np.uint32), order)
+        assert np.array_equal(cs.cpu().numpy().view(np.uint32).astype(np.int64), start)
+
+
+def test_static_sort_rejects_huge_axes_before_forming_the_cell_count(torch_cuda):
+    torch = torch_cuda
+    x1 = torch.zeros((1, 3), dtype=torch.float64, device="cuda")
+    o1 = torch.empty(1, dtype=torch.int32, device="cuda")
+    cs = torch.empty(9, dtype=torch.int32, device="cuda")
+    for dims in ((2 ** 40, 2 ** 40, 2 ** 40), (1, 1, dem.STATIC_SORT_MAX_CELLS + 1), (0, 4, 4)):
+        with pytest.raises(dem.DemError) as e:
+            dem.dem_sort_cells_static(x1, (0, 0, 0), 1.0, dims, o1, o1, cs)
+        assert e.value.status == 1
