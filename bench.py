@@ -733,7 +733,7 @@ def run_ours(args):
         bpp = profiled_traffic_per_particle(p.resort_interval != 1)
         roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": (round(bpp * N) if bpp else None),
-                "kernel": "k_force<PF32,practical,%s>" % ("list" if p.resort_interval != 1 else "walk"), "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "kernel": "k_list<PF32,practical>" if p.resort_interval != 1 else "k_force<PF32,practical>", "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                 "algorithmic_bytes_per_particle": round(b_force, 1), "Z": round(Z, 3), "W": round(W, 4),
                 "force_ms": round(force_ms, 4), "sort_ms": round(sort_ms, 4)}
 
