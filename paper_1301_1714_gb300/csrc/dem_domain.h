@@ -53,6 +53,7 @@ struct Domain {
     uint32_t* ncnt = nullptr;
     uint32_t* nl = nullptr;
     float4* ref = nullptr;         // positions at the last sort
+    uint32_t* wmask = nullptr;     // walls each particle can reach before the next sort (bit w = wall w)
     uint32_t* canon = nullptr;     // (cell, id) position -> pre-sort position, at a sort
     uint32_t* fin = nullptr;       // (cell, id) position -> stored position (window order by contact count)
 
@@ -113,6 +114,7 @@ cudaError_t run_sort_cond(Domain& d, cudaGraphConditionalHandle h);  // graph co
 cudaError_t run_force(Domain& d, bool eval, double* dbgF, double* dbgT);
 // list mode (dem_list.cu): the neighbour lists of a sort, and the force pass over them
 cudaError_t run_lists(Domain& d);
+cudaError_t run_wall_masks(Domain& d);   // the wall masks again (after the walls changed)
 cudaError_t run_force_list(Domain& d, bool eval, double* dbgF, double* dbgT);
 cudaError_t run_export(Domain& d, double* x, double* v, double* w);
 cudaError_t run_diag(Domain& d);   // fills d.diag_out[0..9] (device)

@@ -95,7 +95,7 @@ void free_particle_buffers(Domain& d) {
     d.allocations.clear();
     d.S64[0] = d.S64[1] = StateF64{};
     d.S32[0] = d.S32[1] = StateF32{};
-    d.ncnt = d.nl = nullptr;
+    d.ncnt = d.nl = d.wmask = nullptr;
     d.ref = nullptr;
     d.canon = d.fin = nullptr;
     for (int i = 0; i < 2; ++i) { d.hcnt[i] = nullptr; d.hpid[i] = nullptr; d.hd[i] = nullptr; }
@@ -312,6 +312,7 @@ dem_status alloc_domain(Domain& d, uint32_t n, uint32_t ncells, std::string& err
     if (d.list_mode) {
         AL(d.ncnt, N * 4);
         AL(d.nl, N * 4 * (size_t)DEM_LIST_CAP);
+        AL(d.wmask, N * 4);
         AL(d.ref, N * 16);
         AL(d.canon, N * 4);
         AL(d.fin, N * 4);
@@ -780,6 +781,9 @@ dem_status dem_set_walls(dem_handle* h, int nwalls, const dem_wall* walls) {
         }
         CK(h, cudaMemcpyAsync(d.d_scenes, d.h_scenes.data(), sizeof(SceneDev) * d.h_scenes.size(),
                               cudaMemcpyHostToDevice, d.stream));
+        // list mode: which walls each particle can reach is known from the last sort;
+        // recompute it for the new walls before the next step
+        if (d.list_mode) CK(h, run_wall_masks(d));
         CK(h, cudaStreamSynchronize(d.stream));
     }
     return DEM_OK;
@@ -1182,7 +1186,7 @@ int64_t dem_device_bytes(const dem_handle* h) {
     size_t b = 2 * state + 2 * (N * 4 + N * 4 * M + N * T * 3 * M) + 5 * N * 4 + 2 * C * 4 + (size_t)d.part_cap * 4 +
                (size_t)d.diag_part_cap * 80 + sizeof(StatusDev) + 128 + sizeof(SceneDev) * d.scenes_cap;
     b += (size_t)h->stage_cap * (9 * 8 + 4);
-    if (d.list_mode) b += N * (4 + 4 * (size_t)DEM_LIST_CAP + 16 + 8);
+    if (d.list_mode) b += N * (4 + 4 * (size_t)DEM_LIST_CAP + 4 + 16 + 8);
     return (int64_t)b;
 }
 
@@ -1677,7 +1681,7 @@ int64_t dem_batch_device_bytes(const dem_batch* b) {
     const size_t state = d.precision == 0 ? N * (9 * 8 + 8) : N * (4 * 16 + 4);
     size_t bytes = 2 * state + 2 * (N * 4 + N * 4 * M + N * T * 3 * M) + 5 * N * 4 + 2 * C * 4 +
                    b->stage_cap * 76 + b->map_cap * 4;
-    if (d.list_mode) bytes += N * (4 + 4 * (size_t)DEM_LIST_CAP + 16 + 8);
+    if (d.list_mode) bytes += N * (4 + 4 * (size_t)DEM_LIST_CAP + 4 + 16 + 8);
     return (int64_t)bytes;
 }
 

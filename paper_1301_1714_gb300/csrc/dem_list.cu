@@ -29,6 +29,7 @@
 #endif
 
 
+
 namespace demgb {
 
 template <class PR>
@@ -45,6 +46,7 @@ struct ListArgs {
     const float4* ref;           // positions at the last sort
     int interval;                // sort at least every `interval` steps (0: never forced)
     const uint32_t* perm;
+    const uint32_t* wmask;       // walls each particle can reach until the next sort
     const uint32_t* hin_cnt;     // springs read
     const uint32_t* hin_pid;
     const T* hin_d;
@@ -57,6 +59,31 @@ struct ListArgs {
 };
 
 // ------------------------------------------------------------------ list build
+// Walls the particle can touch before the next sort: walls do not move (their velocity
+// only enters the contact law), and a particle moves less than skin/2 between sorts, so
+// every wall within r + skin/2 (+ the FP32 margin) of it now; bit w marks wall w.
+template <class PR>
+__device__ __forceinline__ uint32_t reachable_walls(const typename PR::Self& me, const SceneDev& S) {
+    typename PR::Self reach = me;
+    reach.r = me.r + (0.5f * S.skin_f + S.eps_f);
+    uint32_t m = 0;
+    for (int w = 0; w < S.nwalls; ++w) {
+        V3<typename PR::T> n, cp;
+        typename PR::T delta;
+        if (PR::wall(S.walls[w], reach, S, n, delta, cp)) m |= 1u << w;
+    }
+    return m;
+}
+
+template <class PR>
+__global__ void __launch_bounds__(256) k_wall_masks(uint32_t n, const SceneDev* scenes, int nscenes,
+                                                    typename PR::State S0, typename PR::State S1, const CtrlDev* ctrl,
+                                                    uint32_t* __restrict__ wmask) {
+    const typename PR::State A = ctrl->cur ? S1 : S0;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
+        wmask[q] = reachable_walls<PR>(PR::load(A, q), scenes[scene_of(scenes, nscenes, q)]);
+}
+
 // Candidates of particle q at a sort: every particle of the 27 cells around q's cell
 // (Eq. 12; list mode numbers the cells brick by brick, so each cell is looked up on its
 // own) within r_i + r_j + skin (+ the FP32 margin), the skin of q's scene. With cells of
@@ -71,7 +98,8 @@ __global__ void __launch_bounds__(256) k_nlist(uint32_t n, const SceneDev* scene
                                                typename PR::State S1, const CtrlDev* ctrl,
                                                const uint32_t* __restrict__ skey, const uint32_t* __restrict__ cs,
                                                const uint32_t* __restrict__ fin, uint32_t* __restrict__ ncnt,
-                                               uint32_t* __restrict__ nl, size_t cap, StatusDev* st) {
+                                               uint32_t* __restrict__ nl, size_t cap, uint32_t* __restrict__ wmask,
+                                               StatusDev* st) {
     if (!ctrl->rebuild) return;
     const typename PR::State A = ctrl->cur ? S1 : S0;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
@@ -109,6 +137,7 @@ __global__ void __launch_bounds__(256) k_nlist(uint32_t n, const SceneDev* scene
         m = min(m, (uint32_t)DEM_LIST_CAP);
         for (uint32_t k = 0; k < m; ++k) nl[(size_t)k * cap + q] = lj[k];
         ncnt[q] = m;
+        wmask[q] = reachable_walls<PR>(me, S);
     }
 }
 
@@ -232,8 +261,9 @@ __global__ void __launch_bounds__(256, DEM_LIST_MIN_BLOCKS) k_list(ListArgs<PR> 
         const typename PR::Self me = PR::load(A, q);
         const Law<T> L = law_of(S, a.stiffness, T());
         const T ri = (T)me.r;
-        // ---- walls (step 8)
-        for (int w = 0; w < S.nwalls; ++w) {
+        // ---- walls (step 8), those the last sort found within reach
+        for (uint32_t wm = __ldg(&a.wmask[q]); wm; wm &= wm - 1) {
+            const int w = __ffs(wm) - 1;
             const WallDev& W = S.walls[w];
             V3<T> n, cp;
             T delta;
@@ -324,10 +354,22 @@ cudaError_t run_lists(Domain& d) {
     if (d.n == 0) return cudaSuccess;
     if (d.precision == 0)
         k_nlist<PF64><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S64[0], d.S64[1], d.ctrl, d.skey,
-                                                          d.cs, d.fin, d.ncnt, d.nl, d.cap, d.st);
+                                                          d.cs, d.fin, d.ncnt, d.nl, d.cap, d.wmask, d.st);
     else
         k_nlist<PF32><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S32[0], d.S32[1], d.ctrl, d.skey,
-                                                          d.cs, d.fin, d.ncnt, d.nl, d.cap, d.st);
+                                                          d.cs, d.fin, d.ncnt, d.nl, d.cap, d.wmask, d.st);
+    DEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
+cudaError_t run_wall_masks(Domain& d) {
+    if (d.n == 0) return cudaSuccess;
+    if (d.precision == 0)
+        k_wall_masks<PF64><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S64[0], d.S64[1], d.ctrl,
+                                                               d.wmask);
+    else
+        k_wall_masks<PF32><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S32[0], d.S32[1], d.ctrl,
+                                                               d.wmask);
     DEM_LAUNCH_CHECK();
     return cudaSuccess;
 }
@@ -351,6 +393,7 @@ static cudaError_t force_list_impl(Domain& d, const typename PR::State& S0, cons
     a.ref = d.ref;
     a.interval = d.interval;
     a.perm = d.perm;
+    a.wmask = d.wmask;
     const int hi = d.h_cur, ho = 1 - d.h_cur;
     a.hin_cnt = d.hcnt[hi];
     a.hin_pid = d.hpid[hi];

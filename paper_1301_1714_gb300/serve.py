@@ -33,7 +33,7 @@ def bytes_per_particle(precision: str = "fp32", max_contacts: int = 32, list_mod
     m = max_contacts or 32
     b = 2 * state + 2 * (4 + 4 * m + t * 3 * m) + 20 + 76 + 4
     if list_mode:
-        b += 4 + 4 * LIST_CAP + 16 + 8
+        b += 4 + 4 * LIST_CAP + 4 + 16 + 8
     return b
 
 
