@@ -1,13 +1,12 @@
-// List mode (re-sort only after some particle moved skin/2): neighbour lists built at a
-// sort, and the force pass that reads them.
+// List mode (re-sort only after some particle moved skin/2): the force pass over the
+// neighbour lists built at each sort (the lists themselves: dem_nlist.cu).
 //
-//   k_nlist  at a sort: every particle of the 27 cells around each particle (Eq. 12)
-//            within r_i + r_j + skin, in the cells' (brick) order
 //   k_list   steps 5-8 and 1 for one thread per stored particle. Phase 1 keeps the list
 //            entries that pass the contact prefilter as a 64-bit mask; phase 2 runs the
 //            lanes of a warp in lockstep over their masks (contact decision, Eq. 1 or
-//            Eqs. 2-10, the spring); then walls (step 8), gravity, the update (step 1)
-//            and the displacement test that decides whether this step ends with a sort.
+//            Eqs. 2-10, the spring); then the walls the last sort found within reach
+//            (step 8), gravity, the update (step 1) and the displacement test that
+//            decides whether this step ends with a sort.
 //
 // Every particle evaluates all of its contacts (each pair twice, once from each side, with
 // arithmetic that makes the two results exact negatives), so a step is one pass with no
@@ -57,89 +56,6 @@ struct ListArgs {
     double* dbgF;
     double* dbgT;
 };
-
-// ------------------------------------------------------------------ list build
-// Walls the particle can touch before the next sort: walls do not move (their velocity
-// only enters the contact law), and a particle moves less than skin/2 between sorts, so
-// every wall within r + skin/2 (+ the FP32 margin) of it now; bit w marks wall w.
-template <class PR>
-__device__ __forceinline__ uint32_t reachable_walls(const typename PR::Self& me, const SceneDev& S) {
-    typename PR::Self reach = me;
-    reach.r = me.r + (0.5f * S.skin_f + S.eps_f);
-    uint32_t m = 0;
-    for (int w = 0; w < S.nwalls; ++w) {
-        V3<typename PR::T> n, cp;
-        typename PR::T delta;
-        if (PR::wall(S.walls[w], reach, S, n, delta, cp)) m |= 1u << w;
-    }
-    return m;
-}
-
-template <class PR>
-__global__ void __launch_bounds__(256) k_wall_masks(uint32_t n, const SceneDev* scenes, int nscenes,
-                                                    typename PR::State S0, typename PR::State S1, const CtrlDev* ctrl,
-                                                    uint32_t* __restrict__ wmask) {
-    const typename PR::State A = ctrl->cur ? S1 : S0;
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
-        wmask[q] = reachable_walls<PR>(PR::load(A, q), scenes[scene_of(scenes, nscenes, q)]);
-}
-
-// Candidates of particle q at a sort: every particle of the 27 cells around q's cell
-// (Eq. 12; list mode numbers the cells brick by brick, so each cell is looked up on its
-// own) within r_i + r_j + skin (+ the FP32 margin), the skin of q's scene. With cells of
-// edge >= 2 r_max + skin no pair that comes into contact before some particle has moved
-// skin/2 is missed. A list is kept in ascending partner id, so the force pass sums a
-// particle's contacts in that order whenever the list was built: results do not depend on
-// when sorts happen (a batch sorts all its scenes together, and each scene still gets the
-// bits of its own run). A list longer than DEM_LIST_CAP is reported (the step returns
-// DEM_ERR_CAPACITY).
-template <class PR>
-__global__ void __launch_bounds__(256) k_nlist(uint32_t n, const SceneDev* scenes, int nscenes, typename PR::State S0,
-                                               typename PR::State S1, const CtrlDev* ctrl,
-                                               const uint32_t* __restrict__ skey, const uint32_t* __restrict__ cs,
-                                               const uint32_t* __restrict__ fin, uint32_t* __restrict__ ncnt,
-                                               uint32_t* __restrict__ nl, size_t cap, uint32_t* __restrict__ wmask,
-                                               StatusDev* st) {
-    if (!ctrl->rebuild) return;
-    const typename PR::State A = ctrl->cur ? S1 : S0;
-    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
-        const SceneDev& S = scenes[scene_of(scenes, nscenes, q)];
-        const typename PR::Self me = PR::load(A, q);
-        const float extra = S.skin_f + S.eps_f;
-        int ix, iy, iz;
-        cell_coords(S, skey[q] - S.c0, ix, iy, iz);
-        uint32_t m = 0;
-        uint32_t lid[DEM_LIST_CAP], lj[DEM_LIST_CAP];   // the list so far, ascending partner id
-        for (int dz = -1; dz <= 1; ++dz)
-            for (int dy = -1; dy <= 1; ++dy)
-                for (int dx = -1; dx <= 1; ++dx) {
-                    const int cx = ix + dx, cy = iy + dy, cz = iz + dz;
-                    if (cx < 0 || cy < 0 || cz < 0 || cx >= S.dims[0] || cy >= S.dims[1] || cz >= S.dims[2]) continue;
-                    const uint32_t c = S.c0 + cell_index(S, (uint32_t)cx, (uint32_t)cy, (uint32_t)cz);
-                    const uint32_t c1 = __ldg(&cs[c + 1]);
-                    for (uint32_t jc = __ldg(&cs[c]); jc < c1; ++jc) {
-                        const uint32_t j = fin[jc];   // the cell table holds (cell, id) positions
-                        if (j == q || !PR::within(A, me, j, extra)) continue;
-                        if (m < DEM_LIST_CAP) {
-                            const uint32_t idj = __ldg(&A.id[j]);
-                            uint32_t k = m;
-                            for (; k > 0 && lid[k - 1] > idj; --k) {
-                                lid[k] = lid[k - 1];
-                                lj[k] = lj[k - 1];
-                            }
-                            lid[k] = idj;
-                            lj[k] = j;
-                        }
-                        ++m;
-                    }
-                }
-        if (m > DEM_LIST_CAP) raise_status(st, ST_LIST, (int32_t)q);
-        m = min(m, (uint32_t)DEM_LIST_CAP);
-        for (uint32_t k = 0; k < m; ++k) nl[(size_t)k * cap + q] = lj[k];
-        ncnt[q] = m;
-        wmask[q] = reachable_walls<PR>(me, S);
-    }
-}
 
 // ------------------------------------------------------------------- force pass
 
@@ -339,9 +255,6 @@ __global__ void __launch_bounds__(256, DEM_LIST_MIN_BLOCKS) k_list(ListArgs<PR> 
 
 // ======================================================================= launchers
 static inline uint32_t nblk(uint32_t n, uint32_t b) { return (n + b - 1) / b; }
-static inline uint32_t sgrid(const Domain& d, uint32_t n) {
-    return std::max(1u, std::min(nblk(n, 256), (uint32_t)std::max(d.sort_blocks, 1)));
-}
 
 #define DEM_LAUNCH_CHECK()                          \
     do {                                            \
@@ -349,30 +262,6 @@ static inline uint32_t sgrid(const Domain& d, uint32_t n) {
         cudaError_t e_ = cudaGetLastError();        \
         if (e_ != cudaSuccess) return e_;           \
     } while (0)
-
-cudaError_t run_lists(Domain& d) {
-    if (d.n == 0) return cudaSuccess;
-    if (d.precision == 0)
-        k_nlist<PF64><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S64[0], d.S64[1], d.ctrl, d.skey,
-                                                          d.cs, d.fin, d.ncnt, d.nl, d.cap, d.wmask, d.st);
-    else
-        k_nlist<PF32><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S32[0], d.S32[1], d.ctrl, d.skey,
-                                                          d.cs, d.fin, d.ncnt, d.nl, d.cap, d.wmask, d.st);
-    DEM_LAUNCH_CHECK();
-    return cudaSuccess;
-}
-
-cudaError_t run_wall_masks(Domain& d) {
-    if (d.n == 0) return cudaSuccess;
-    if (d.precision == 0)
-        k_wall_masks<PF64><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S64[0], d.S64[1], d.ctrl,
-                                                               d.wmask);
-    else
-        k_wall_masks<PF32><<<sgrid(d, d.n), 256, 0, d.stream>>>(d.n, d.d_scenes, d.nscenes, d.S32[0], d.S32[1], d.ctrl,
-                                                               d.wmask);
-    DEM_LAUNCH_CHECK();
-    return cudaSuccess;
-}
 
 template <class PR>
 static cudaError_t force_list_impl(Domain& d, const typename PR::State& S0, const typename PR::State& S1, bool eval,
