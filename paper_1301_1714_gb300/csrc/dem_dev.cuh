@@ -18,9 +18,11 @@
 // Neighbour lists of list mode: at most DEM_LIST_CAP candidates per particle (one bit each
 // in the force pass's 64-bit mask); a fuller list is reported, never truncated silently.
 #define DEM_LIST_CAP 64
-// Cell order of list mode: bricks of 2^s x 2^s x 2^s cells (0 = row-major).
+// Cell order of list mode: bricks of 2^s x 2^s x 2^s cells, s at most DEM_LIST_BRICK_SHIFT
+// (0 = row-major). Each grid takes the largest s whose padding to whole bricks adds at most
+// 1/8 to its cell count.
 #ifndef DEM_LIST_BRICK_SHIFT
-#define DEM_LIST_BRICK_SHIFT 2
+#define DEM_LIST_BRICK_SHIFT 4
 #endif
 
 namespace demgb {
