@@ -169,7 +169,10 @@ dem_status dem_create(const dem_config* cfg, int device, void* cuda_stream, dem_
 /* Sets n particles (Sec. 3 particle properties): positions x, velocities v, spins w
  * (3n doubles each, id order) and radii r (n floats, > 0). id must be NULL: particle k
  * has global id k. Clears the tangential history. Allocates device memory as needed
- * and performs the first cell sort (steps 2-4). n may be 0. */
+ * and performs the first cell sort (steps 2-4). n may be 0. The arrays are checked on
+ * the device, host and device inputs alike (host inputs after their upload):
+ * DEM_ERR_INVALID_ARG for a radius that is not finite and > 0 or a non-finite x, v or w,
+ * and the handle then holds no particles. */
 dem_status dem_set_particles(dem_handle* h, int64_t n, const uint32_t* id, const double* x, const double* v,
                              const double* w, const float* r, int where);
 

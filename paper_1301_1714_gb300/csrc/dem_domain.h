@@ -107,6 +107,9 @@ struct StepGraph {
 
 // -------- launchers (dem_kernels.cu); all enqueue on d.stream and count launches
 cudaError_t run_import(Domain& d, const double* x, const double* v, const double* w, const float* r);
+// out[0]: 1 = a radius not finite and > 0, 2 = a non-finite x, v or w; out[1]: bits of r_max
+cudaError_t run_check_input(Domain& d, uint32_t n, const double* x, const double* v, const double* w, const float* r,
+                            uint32_t* out);
 cudaError_t run_hash(Domain& d);      // cell key + in-cell rank of the next state (if sorting)
 cudaError_t run_rebuild(Domain& d);   // scan, scatter, (cell, id) gather, lists (if sorting)
 cudaError_t run_end_step(Domain& d);  // step bookkeeping (swap or keep, counters)

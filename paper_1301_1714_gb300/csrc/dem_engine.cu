@@ -45,6 +45,9 @@ struct dem_handle {
     double* stage = nullptr;
     float* stage_r = nullptr;
     uint32_t stage_cap = 0;
+    // input check of dem_set_particles: flags and the largest radius (device, pinned host)
+    uint32_t* chk_dev = nullptr;
+    uint32_t* chk_host = nullptr;
 };
 
 namespace {
@@ -465,26 +468,35 @@ dem_status load_particles(dem_handle* h, int64_t n64, const double* x, const dou
     if (where != DEM_HOST && where != DEM_DEVICE) return fail(h, DEM_ERR_INVALID_ARG, "where");
     h->graph.reset();
     if (n > 0 && (!x || !v || !w || !r)) return fail(h, DEM_ERR_INVALID_ARG, "x, v, w and r are required");
-    // radii (and, for host input, positions) are checked on the host
-    std::vector<float> rh;
-    const float* rr = r;
-    if (n > 0 && where == DEM_DEVICE) {
-        rh.resize(n);
-        CK(h, cudaMemcpy(rh.data(), r, (size_t)n * 4, cudaMemcpyDeviceToHost));
-        rr = rh.data();
-    }
+    // host input goes to the staging buffers first; the arrays are checked (radii finite
+    // and > 0, finite x, v, w) and r_max is found on the device, before anything of the
+    // handle's state changes
+    const double *xd = x, *vd = v, *wd = w;
+    const float* rd = r;
     double rmax = 0.0;
-    for (uint32_t k = 0; k < n; ++k) {
-        if (!(rr[k] > 0.f) || !std::isfinite(rr[k])) return fail(h, DEM_ERR_INVALID_ARG, "radii must be finite and > 0");
-        rmax = std::max(rmax, (double)rr[k]);
+    dem_status s;
+    if (n > 0) {
+        if (where == DEM_HOST) {
+            s = ensure_stage(h, n);
+            if (s != DEM_OK) return s;
+            CK(h, cudaMemcpyAsync(h->stage, x, (size_t)n * 24, cudaMemcpyHostToDevice, d.stream));
+            CK(h, cudaMemcpyAsync(h->stage + 3 * (size_t)n, v, (size_t)n * 24, cudaMemcpyHostToDevice, d.stream));
+            CK(h, cudaMemcpyAsync(h->stage + 6 * (size_t)n, w, (size_t)n * 24, cudaMemcpyHostToDevice, d.stream));
+            CK(h, cudaMemcpyAsync(h->stage_r, r, (size_t)n * 4, cudaMemcpyHostToDevice, d.stream));
+            xd = h->stage; vd = h->stage + 3 * (size_t)n; wd = h->stage + 6 * (size_t)n; rd = h->stage_r;
+        }
+        CK(h, run_check_input(d, n, xd, vd, wd, rd, h->chk_dev));
+        CK(h, cudaMemcpyAsync(h->chk_host, h->chk_dev, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, d.stream));
+        CK(h, cudaStreamSynchronize(d.stream));
+        if (h->chk_host[0] & 1u) return fail(h, DEM_ERR_INVALID_ARG, "radii must be finite and > 0");
+        if (h->chk_host[0] & 2u) return fail(h, DEM_ERR_INVALID_ARG, "non-finite position, velocity or spin in the input");
+        float rm;
+        std::memcpy(&rm, &h->chk_host[1], sizeof rm);
+        rmax = (double)rm;
     }
-    if (where == DEM_HOST)
-        for (uint32_t k = 0; k < n; ++k)
-            if (!finite3(x + 3 * (size_t)k) || !finite3(v + 3 * (size_t)k) || !finite3(w + 3 * (size_t)k))
-                return fail(h, DEM_ERR_INVALID_ARG, "non-finite position, velocity or spin in the input");
     const dem_config& c = h->cfg;
     int64_t nc = 1;
-    dem_status s = set_grid(h, n > 0, rmax, nc);
+    s = set_grid(h, n > 0, rmax, nc);
     if (s != DEM_OK) return s;
     d.n = n;
     d.ncells = (uint32_t)nc;
@@ -512,17 +524,6 @@ dem_status load_particles(dem_handle* h, int64_t n64, const double* x, const dou
     if (n > 0) {
         CK(h, cudaMemsetAsync(d.hcnt[0], 0, (size_t)n * 4, d.stream));
         CK(h, cudaMemsetAsync(d.hcnt[1], 0, (size_t)n * 4, d.stream));
-        const double *xd = x, *vd = v, *wd = w;
-        const float* rd = r;
-        if (where == DEM_HOST) {
-            s = ensure_stage(h, n);
-            if (s != DEM_OK) return s;
-            CK(h, cudaMemcpyAsync(h->stage, x, (size_t)n * 24, cudaMemcpyHostToDevice, d.stream));
-            CK(h, cudaMemcpyAsync(h->stage + 3 * (size_t)n, v, (size_t)n * 24, cudaMemcpyHostToDevice, d.stream));
-            CK(h, cudaMemcpyAsync(h->stage + 6 * (size_t)n, w, (size_t)n * 24, cudaMemcpyHostToDevice, d.stream));
-            CK(h, cudaMemcpyAsync(h->stage_r, r, (size_t)n * 4, cudaMemcpyHostToDevice, d.stream));
-            xd = h->stage; vd = h->stage + 3 * (size_t)n; wd = h->stage + 6 * (size_t)n; rd = h->stage_r;
-        }
         CK(h, run_import(d, xd, vd, wd, rd));
         CK(h, run_hash(d));
         CK(h, run_rebuild(d));
@@ -757,6 +758,8 @@ dem_status dem_create(const dem_config* cfg, int device, void* cuda_stream, dem_
         cudaMallocHost(&d.ctrl_host, sizeof(CtrlDev)) != cudaSuccess ||
         cudaMemset(d.ctrl, 0, sizeof(CtrlDev)) != cudaSuccess ||
         cudaMalloc(&d.diag_out, 16 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&h->chk_dev, 2 * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&h->chk_host, 2 * sizeof(uint32_t)) != cudaSuccess ||
         cudaMemset(d.st, 0, sizeof(StatusDev)) != cudaSuccess) {
         cudaGetLastError();
         dem_destroy(h);
@@ -1241,6 +1244,8 @@ void dem_destroy(dem_handle* h) {
     if (h->d.ctrl) cudaFree(h->d.ctrl);
     if (h->d.ctrl_host) cudaFreeHost(h->d.ctrl_host);
     if (h->d.diag_out) cudaFree(h->d.diag_out);
+    if (h->chk_dev) cudaFree(h->chk_dev);
+    if (h->chk_host) cudaFreeHost(h->chk_host);
     if (h->stage) cudaFree(h->stage);
     if (h->stage_r) cudaFree(h->stage_r);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);

@@ -716,6 +716,40 @@ static inline uint32_t sgrid(const Domain& d, uint32_t n) {
         if (e_ != cudaSuccess) return e_;           \
     } while (0)
 
+// Input check of dem_set_particles on the device (the arrays are there anyway, and a
+// host loop over them costs ~20 ms per 4M particles on one core): out[0] |= 1 for a radius
+// that is not finite and > 0, |= 2 for a non-finite position, velocity or spin; out[1] =
+// bits of the largest radius (radii are positive, so their bits order like their values).
+__global__ void __launch_bounds__(256) k_check_input(uint32_t n, const double* __restrict__ x,
+                                                     const double* __restrict__ v, const double* __restrict__ w,
+                                                     const float* __restrict__ r, uint32_t* out) {
+    uint32_t bad = 0, rmax = 0;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
+        const float rq = r[q];
+        if (!(rq > 0.f) || !isfinite(rq)) bad |= 1u;
+        else rmax = max(rmax, __float_as_uint(rq));
+        for (int c = 0; c < 3; ++c) {
+            const size_t o = 3 * (size_t)q + c;
+            if (!isfinite(x[o]) || !isfinite(v[o]) || !isfinite(w[o])) bad |= 2u;
+        }
+    }
+    bad = __reduce_or_sync(0xffffffffu, bad);
+    rmax = __reduce_max_sync(0xffffffffu, rmax);
+    if ((threadIdx.x & 31u) == 0) {
+        if (bad) atomicOr(&out[0], bad);
+        if (rmax) atomicMax(&out[1], rmax);
+    }
+}
+
+cudaError_t run_check_input(Domain& d, uint32_t n, const double* x, const double* v, const double* w, const float* r,
+                            uint32_t* out) {
+    cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(uint32_t), d.stream);
+    if (e != cudaSuccess || n == 0) return e;
+    k_check_input<<<sgrid(d, n), 256, 0, d.stream>>>(n, x, v, w, r, out);
+    DEM_LAUNCH_CHECK();
+    return cudaSuccess;
+}
+
 cudaError_t run_import(Domain& d, const double* x, const double* v, const double* w, const float* r) {
     // the caller has set ctrl->cur = 0, so set 1 is the "next" set that the sort gathers from
     if (d.n == 0) return cudaSuccess;

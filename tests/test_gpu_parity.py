@@ -449,6 +449,41 @@ def test_invalid_inputs_are_rejected():
         dem.dem_destroy(h)
 
 
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_input_check_on_the_device(where):
+    """dem_set_particles checks its arrays on the device, host and device inputs alike:
+    each kind of bad value (first, middle and last particle) is rejected with its reason,
+    and a good call after a rejected one gives the oracle's run."""
+    import torch
+    sc = scenes.box_lattice(seed=2)
+    n = sc.n
+    bad = [("x", (0, 2), np.inf, "non-finite"), ("v", (n // 2, 0), np.nan, "non-finite"),
+           ("w", (n - 1, 1), -np.inf, "non-finite"), ("r", 0, np.nan, "radii"), ("r", n // 3, -1e-3, "radii"),
+           ("r", n - 1, np.inf, "radii"), ("r", 5, 0.0, "radii")]
+    h = dem.dem_create(dem.config_from_params(sc.params))
+    try:
+        dem.dem_set_walls(h, sc.params.walls)
+        for name, idx, val, why in bad:
+            a = {"x": sc.x.copy(), "v": sc.v.copy(), "w": sc.w.copy(), "r": sc.r.copy()}
+            a[name][idx] = val
+            args = [a["x"], a["v"], a["w"], a["r"]]
+            if where == "device":
+                args = [torch.tensor(t, device="cuda:0") for t in args]
+            with pytest.raises(dem.DemError) as e:
+                dem.dem_set_particles(h, *args)
+            assert e.value.status == dem.DEM_ERR_INVALID_ARG and why in str(e.value), (name, idx, str(e.value))
+        args = [sc.x, sc.v, sc.w, sc.r]
+        if where == "device":
+            args = [torch.tensor(t, device="cuda:0") for t in args]
+        dem.dem_set_particles(h, *args)
+        dem.dem_step(h, 20)
+        x, _, _ = dem.dem_get_state(h, n)
+    finally:
+        dem.dem_destroy(h)
+    ref = oracle.State(sc.params, sc.x, sc.v, sc.w, sc.r).run(20)
+    assert np.max(np.abs(x - ref.x)) <= 1e-12
+
+
 def test_device_pointer_inputs_and_outputs():
     import torch
     sc = scenes.box_lattice(seed=7)
