@@ -41,7 +41,8 @@ typedef enum {
     DEM_ERR_INVALID_ARG = 1,  /* a pointer, size or parameter is out of range */
     DEM_ERR_OOM = 2,          /* a device or host allocation failed */
     DEM_ERR_CUDA = 3,         /* a CUDA runtime call failed */
-    DEM_ERR_CAPACITY = 4,     /* a particle had more contacts than max_contacts */
+    DEM_ERR_CAPACITY = 4,     /* a particle had more contacts than 64 (or, for batches and
+                                 slabs, than max_contacts), or a neighbour list overflowed */
     DEM_ERR_TIMEOUT = 5,      /* a bounded device-side wait gave up */
     DEM_ERR_NONFINITE = 6,    /* a position or velocity became NaN/Inf */
     DEM_ERR_STATE = 7         /* call order: e.g. dem_step before dem_set_particles */
@@ -108,10 +109,14 @@ enum { DEM_TERM_NO_ATTRACTION = 1, DEM_TERM_ROLLING = 2, DEM_TERM_ETA_T = 4, DEM
  *  mu_roll     rolling resistance coefficient (DEM_TERM_ROLLING)
  *  alpha_t     tangential damping factor (DEM_TERM_ETA_T)
  *  k_coh       cohesion energy density [N/m^2] (DEM_TERM_COHESION)
- *  max_contacts  per-particle capacity of the contact/history list (incl. walls);
- *              0 = 32. Neighbour lists (resort_interval != 1) hold 64 candidates
- *              whatever max_contacts is. Exceeding either makes dem_step return
- *              DEM_ERR_CAPACITY; no contact is dropped silently.
+ *  max_contacts  starting per-particle capacity of the contact/history list (incl.
+ *              walls); 0 = 32. A step in which a particle has more contacts is voided
+ *              on the device and dem_step runs it again with twice the capacity, up to
+ *              64 (a handle keeps the capacity it grew to); past 64 dem_step returns
+ *              DEM_ERR_CAPACITY. Batches and slabs keep max_contacts and report an
+ *              overflow. Neighbour lists (resort_interval != 1) hold 64 candidates
+ *              whatever max_contacts is; a fuller list makes dem_step return
+ *              DEM_ERR_CAPACITY. No contact is dropped silently.
  */
 typedef struct {
     int32_t model;
@@ -180,9 +185,11 @@ dem_status dem_set_particles(dem_handle* h, int64_t n, const uint32_t* id, const
 dem_status dem_set_walls(dem_handle* h, int nwalls, const dem_wall* walls);
 
 /* Advances nsteps timesteps (each: forces of steps 5-8 at the current state, update of
- * step 1, then steps 2-4 for the new positions). Returns the first error raised on the
- * device during these steps (DEM_ERR_CAPACITY, DEM_ERR_NONFINITE), after which the state
- * is the one reached when the error was detected at the end of the call. */
+ * step 1, then steps 2-4 for the new positions). A step that overflows the contact
+ * capacity is voided and run again with the capacity doubled (see max_contacts); if 64
+ * contacts are still too few, DEM_ERR_CAPACITY is returned with the state from before
+ * that step. Other errors raised on the device (DEM_ERR_NONFINITE, a full neighbour
+ * list) are returned with the state reached at the end of the call. */
 dem_status dem_step(dem_handle* h, int64_t nsteps);
 
 /* Runs until the particles come to rest: the paper continues its benchmark until every
@@ -393,8 +400,8 @@ void dem_slabs_destroy(dem_slabs* s);
 int64_t dem_device_bytes(const dem_handle* h);
 
 /* Largest number of contacts (particles and walls) of any one particle in the last
- * step, as read at the end of the last dem_step; dem_config.max_contacts must stay
- * above it (a step that exceeds the capacity fails with DEM_ERR_CAPACITY). */
+ * step, as read at the end of the last dem_step (at most the handle's capacity, which
+ * dem_step grows up to 64 as needed). */
 int64_t dem_max_contacts_seen(const dem_handle* h);
 
 /* Number of kernel launches the handle has enqueued so far (kernels that a replayed step

@@ -86,17 +86,22 @@ struct StatusDev {
 };
 
 enum : int32_t { ST_OK = 0, ST_CAPACITY = 4, ST_LIST = 5, ST_NONFINITE = 6 };
+#define DEM_HALT 2
 
 // Step control, read and written only by kernels (the host never needs to know, while
 // stepping, whether a step sorted).
 struct CtrlDev {
     int32_t cur;         // state set holding the current cell-sorted state (the other is "next")
-    int32_t rebuild;     // 1: this step ends with a cell sort (and, in list mode, new lists)
+    int32_t rebuild;     // bit 0: this step ends with a cell sort (and, in list mode, new lists);
+                         // bit 1 (DEM_HALT): a particle overflowed its contact slots this step, so
+                         // the step is void: no sort, no swap, and the later steps of the launch
+                         // sequence do nothing (the host grows the slots and runs it again)
     int32_t perm_valid;  // 1: the last step sorted, so stored springs are read through perm
     int32_t since;       // steps since the last sort
     uint32_t nsorts;     // sorts performed since the particles were set
     uint32_t cond_sorts; // sorts run as the conditional body of a step graph (launch accounting)
-    int32_t pad[2];
+    uint32_t steps_done; // steps completed (not void) since the control block was set
+    int32_t pad;
 };
 
 __device__ __forceinline__ void raise_status(StatusDev* st, int32_t code, int32_t where) {

@@ -27,6 +27,8 @@ struct Domain {
     int stiffness = 0;   // 0 linear, 1 Hertz
     int maxc = 32;       // history slots per particle
     int block = 128;     // force kernel block size
+    int regrow = 0;      // 1: a contact-slot overflow voids the step (the handle grows its slots
+                         // and runs the step again); 0: it is only reported
     cudaStream_t stream = nullptr;
 
     // sizes

@@ -45,7 +45,8 @@ struct dem_handle {
     double* stage = nullptr;
     float* stage_r = nullptr;
     uint32_t stage_cap = 0;
-    // input check of dem_set_particles: flags and the largest radius (device, pinned host)
+    // input check of dem_set_particles: flags and the largest radius (device, pinned host);
+    // chk_host[2]: the device's count of completed steps when a dem_step attempt began
     uint32_t* chk_dev = nullptr;
     uint32_t* chk_host = nullptr;
 };
@@ -399,6 +400,47 @@ dem_status read_ctrl(dem_handle* h, CtrlDev& c) {
     return DEM_OK;
 }
 
+// Contact slots of a handle grown to newmaxc: new history buffers, the springs of the
+// buffer the next step reads copied in (the partner-id planes keep their places; the
+// three component blocks move to the new stride); the other buffer is written by the
+// next step. On failure the old buffers stay.
+dem_status regrow_slots(dem_handle* h, int newmaxc) {
+    Domain& d = h->d;
+    const size_t N = d.cap, M = (size_t)d.maxc, M2 = (size_t)newmaxc;
+    const size_t T = d.precision == 0 ? sizeof(double) : sizeof(float);
+    void* npid[2] = {nullptr, nullptr};
+    void* nhd[2] = {nullptr, nullptr};
+    bool ok = true;
+    for (int s = 0; s < 2 && ok; ++s)
+        ok = cudaMalloc(&npid[s], N * 4 * M2) == cudaSuccess && cudaMalloc(&nhd[s], N * T * 3 * M2) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        for (int s = 0; s < 2; ++s) {
+            if (npid[s]) cudaFree(npid[s]);
+            if (nhd[s]) cudaFree(nhd[s]);
+        }
+        return fail(h, DEM_ERR_OOM, "cudaMalloc of the grown contact slots failed");
+    }
+    const int hi = d.h_cur;
+    CK(h, cudaMemcpyAsync(npid[hi], d.hpid[hi], N * 4 * M, cudaMemcpyDeviceToDevice, d.stream));
+    for (size_t c = 0; c < 3; ++c)
+        CK(h, cudaMemcpyAsync((char*)nhd[hi] + c * M2 * N * T, (const char*)d.hd[hi] + c * M * N * T, M * N * T,
+                              cudaMemcpyDeviceToDevice, d.stream));
+    CK(h, cudaStreamSynchronize(d.stream));
+    for (int s = 0; s < 2; ++s) {
+        for (void*& p : d.allocations) {
+            if (p == (void*)d.hpid[s]) p = npid[s];
+            else if (p == d.hd[s]) p = nhd[s];
+        }
+        cudaFree(d.hpid[s]);
+        cudaFree(d.hd[s]);
+        d.hpid[s] = (uint32_t*)npid[s];
+        d.hd[s] = nhd[s];
+    }
+    d.maxc = newmaxc;
+    return DEM_OK;
+}
+
 dem_status rotate_counters(dem_handle* h) {
     Domain& d = h->d;
     CK(h, cudaMemcpyAsync(&d.st->last, &d.st->live, sizeof(CountersDev), cudaMemcpyDeviceToDevice, d.stream));
@@ -749,6 +791,7 @@ dem_status dem_create(const dem_config* cfg, int device, void* cuda_stream, dem_
     d.block = cfg->block_size > 0 ? cfg->block_size : 256;
     d.sort_blocks = sort_blocks_of(device);
     d.list_mode = cfg->resort_interval != 1 ? 1 : 0;
+    d.regrow = 1;   // a contact-slot overflow voids the step; dem_step grows the slots and reruns it
     d.interval = cfg->resort_interval;
     d.maxn = DEM_LIST_CAP;
     d.stream = (cudaStream_t)cuda_stream;
@@ -759,7 +802,7 @@ dem_status dem_create(const dem_config* cfg, int device, void* cuda_stream, dem_
         cudaMemset(d.ctrl, 0, sizeof(CtrlDev)) != cudaSuccess ||
         cudaMalloc(&d.diag_out, 16 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&h->chk_dev, 2 * sizeof(uint32_t)) != cudaSuccess ||
-        cudaMallocHost(&h->chk_host, 2 * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMallocHost(&h->chk_host, 4 * sizeof(uint32_t)) != cudaSuccess ||
         cudaMemset(d.st, 0, sizeof(StatusDev)) != cudaSuccess) {
         cudaGetLastError();
         dem_destroy(h);
@@ -817,52 +860,98 @@ dem_status dem_step(dem_handle* h, int64_t nsteps) {
     DeviceGuard g(h->device);
     Domain& d = h->d;
     const bool timed = h->timing && d.n > 0;
-    if (timed) {
-        const size_t need = 3 * (size_t)nsteps;
-        while (h->events.size() < need) {
-            cudaEvent_t e;
-            CK(h, cudaEventCreate(&e));
-            h->events.push_back(e);
-        }
-    }
-    if (timed) {
-        // list mode on a capturable stream: the sort tail runs as a small graph whose sort
-        // node executes only when the device decided to sort
-        if (d.list_mode && d.stream && !h->graph.sort_exec[0] && capture_sort_graphs(d, &h->graph) != cudaSuccess)
-            cudaGetLastError();
-        for (int64_t s = 0; s < nsteps; ++s) {
-            CK(h, cudaEventRecord(h->events[3 * s], d.stream));
-            CK(h, run_force(d, false, nullptr, nullptr));
-            CK(h, cudaEventRecord(h->events[3 * s + 1], d.stream));
-            d.h_cur = 1 - d.h_cur;
-            if (h->graph.sort_exec[d.h_cur]) {
-                CK(h, cudaGraphLaunch(h->graph.sort_exec[d.h_cur], d.stream));
-                d.launches += h->graph.sort_launches;
-            } else {
-                if (d.list_mode) CK(h, run_hash(d));   // (sort steps only; fused into the force pass otherwise)
-                CK(h, run_rebuild(d));
-                CK(h, run_end_step(d));
+    int64_t left = nsteps;
+    for (;;) {
+        if (timed) {
+            const size_t need = 3 * (size_t)left;
+            while (h->events.size() < need) {
+                cudaEvent_t e;
+                CK(h, cudaEventCreate(&e));
+                h->events.push_back(e);
             }
-            CK(h, cudaEventRecord(h->events[3 * s + 2], d.stream));
         }
-    } else {
-        CK(h, run_steps(d, &h->graph, nsteps));
-    }
-    h->steps += nsteps;
-    if (nsteps > 0) h->eval_valid = false;
-    dem_status st = sync_status(h);
-    if (timed) {
-        for (int64_t s = 0; s < nsteps; ++s) {
-            float a = 0.f, b = 0.f;
-            CK(h, cudaEventElapsedTime(&a, h->events[3 * s], h->events[3 * s + 1]));
-            CK(h, cudaEventElapsedTime(&b, h->events[3 * s + 1], h->events[3 * s + 2]));
-            h->t_force_ms += a;
-            h->t_sort_ms += b;
+        // the device's count of completed steps as this attempt begins (read back with the
+        // status, so that a void step can be located without another synchronisation)
+        const int hc0 = d.h_cur;
+        CK(h, cudaMemcpyAsync(&h->chk_host[2], &d.ctrl->steps_done, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                              d.stream));
+        if (timed) {
+            // list mode on a capturable stream: the sort tail runs as a small graph whose sort
+            // node executes only when the device decided to sort
+            if (d.list_mode && d.stream && !h->graph.sort_exec[0] && capture_sort_graphs(d, &h->graph) != cudaSuccess)
+                cudaGetLastError();
+            for (int64_t s = 0; s < left; ++s) {
+                CK(h, cudaEventRecord(h->events[3 * s], d.stream));
+                CK(h, run_force(d, false, nullptr, nullptr));
+                CK(h, cudaEventRecord(h->events[3 * s + 1], d.stream));
+                d.h_cur = 1 - d.h_cur;
+                if (h->graph.sort_exec[d.h_cur]) {
+                    CK(h, cudaGraphLaunch(h->graph.sort_exec[d.h_cur], d.stream));
+                    d.launches += h->graph.sort_launches;
+                } else {
+                    if (d.list_mode) CK(h, run_hash(d));   // (sort steps only; fused into the force pass otherwise)
+                    CK(h, run_rebuild(d));
+                    CK(h, run_end_step(d));
+                }
+                CK(h, cudaEventRecord(h->events[3 * s + 2], d.stream));
+            }
+        } else {
+            CK(h, run_steps(d, &h->graph, left));
         }
-        h->n_force += nsteps;
-        h->n_sort += nsteps;
+        dem_status st = sync_status(h);
+        // a particle with more contacts than slots voided its step (and the later ones of
+        // this attempt did nothing): the state is the one at the start of that step
+        int64_t done = left;
+        bool void_step = false;
+        if (st == DEM_ERR_CAPACITY && d.st_host->code == ST_CAPACITY && d.regrow) {
+            CtrlDev c;
+            dem_status s2 = read_ctrl(h, c);
+            if (s2 != DEM_OK) return s2;
+            if (c.rebuild & DEM_HALT) {
+                void_step = true;
+                done = (int64_t)(uint32_t)(c.steps_done - h->chk_host[2]);
+            }
+        }
+        h->steps += done;
+        if (done > 0) h->eval_valid = false;
+        if (timed) {
+            for (int64_t s = 0; s < done; ++s) {
+                float a = 0.f, b = 0.f;
+                CK(h, cudaEventElapsedTime(&a, h->events[3 * s], h->events[3 * s + 1]));
+                CK(h, cudaEventElapsedTime(&b, h->events[3 * s + 1], h->events[3 * s + 2]));
+                h->t_force_ms += a;
+                h->t_sort_ms += b;
+            }
+            h->n_force += done;
+            h->n_sort += done;
+        }
+        if (!void_step) return st;
+        // resume at the void step: its history buffers (the parity of the steps done), the
+        // step control as at its start, no counters, no cell counts of its new keys
+        d.h_cur = hc0 ^ (int)(done & 1);
+        CtrlDev c;
+        CK(h, cudaMemcpyAsync(&c, d.ctrl, sizeof c, cudaMemcpyDeviceToHost, d.stream));
+        CK(h, cudaStreamSynchronize(d.stream));
+        c.rebuild = d.list_mode ? 0 : 1;
+        *d.ctrl_host = c;
+        CK(h, cudaMemcpyAsync(d.ctrl, d.ctrl_host, sizeof(CtrlDev), cudaMemcpyHostToDevice, d.stream));
+        CK(h, cudaMemsetAsync(&d.st->live, 0, sizeof(CountersDev), d.stream));
+        CK(h, cudaMemsetAsync(d.cnt, 0, ((size_t)d.ncells + 1) * 4, d.stream));
+        CK(h, cudaStreamSynchronize(d.stream));
+        h->graph.reset();
+        if (d.maxc >= 64) {
+            char buf[200];
+            snprintf(buf, sizeof buf,
+                     "particle at sorted position %d has more than 64 contacts (the largest capacity); the state is "
+                     "the one before the step that overflowed",
+                     d.st_host->where);
+            return fail(h, DEM_ERR_CAPACITY, buf);
+        }
+        const dem_status sg = regrow_slots(h, std::min(64, 2 * d.maxc));
+        if (sg != DEM_OK) return sg;
+        h->err.clear();
+        left -= done;
     }
-    return st;
 }
 
 dem_status dem_run_until(dem_handle* h, int64_t max_steps, double disp_threshold, int64_t check_every,
@@ -1986,6 +2075,7 @@ dem_status dem_slabs_create(const dem_config* cfg, int nslabs, int axis, int dev
             dem_slabs_destroy(S);
             return st;
         }
+        h->d.regrow = 0;   // a slab's overflow is reported (its step is part of the exchange)
         S->sl.push_back(h);
     }
     S->cur.assign(nslabs, 0);

@@ -53,6 +53,7 @@ struct ForceArgs {
     StatusDev* st;
     double* dbgF;
     double* dbgT;
+    int halt;                    // 1: a capacity overflow makes the step void (DEM_HALT)
 };
 
 
@@ -70,6 +71,8 @@ __global__ void __launch_bounds__(256, DEM_FORCE_MIN_BLOCKS) k_force(ForceArgs<P
     constexpr bool PRACT = MODEL != 1;
     constexpr bool TERMS = MODEL == 2;
     extern __shared__ uint32_t smem[];
+    // a void step (an earlier launch overflowed): nothing to do; one decision per warp
+    if (!EVAL && __any_sync(0xffffffffu, (a.ctrl->rebuild & DEM_HALT) != 0)) return;
     const int cur = a.ctrl->cur;
     const typename PR::State A = cur ? a.S1 : a.S0;
     const typename PR::State B = cur ? a.S0 : a.S1;
@@ -139,7 +142,10 @@ __global__ void __launch_bounds__(256, DEM_FORCE_MIN_BLOCKS) k_force(ForceArgs<P
 #pragma unroll
         for (int r = 0; r < 9; ++r)
             PR::scan_row(A, me, S, rlo[r], rhi[r], q, s_near, bd, tid, maxc, nnear);
-        if (nnear > maxc) raise_status(a.st, ST_CAPACITY, (int32_t)q);
+        if (nnear > maxc) {
+            raise_status(a.st, ST_CAPACITY, (int32_t)q);
+            if (!EVAL && a.halt) atomicOr(&a.ctrl->rebuild, DEM_HALT);
+        }
     }
     // ---- phase 2: contacts, in lockstep over the lists
     const uint32_t mylen = min(nnear, maxc);
@@ -223,7 +229,10 @@ __global__ void __launch_bounds__(256, DEM_FORCE_MIN_BLOCKS) k_force(ForceArgs<P
             ++c_wc;
             c_maxov = fmaxf(c_maxov, (float)delta);
         }
-        if (nnew > maxc) raise_status(a.st, ST_CAPACITY, (int32_t)q);
+        if (nnew > maxc) {
+            raise_status(a.st, ST_CAPACITY, (int32_t)q);
+            if (!EVAL && a.halt) atomicOr(&a.ctrl->rebuild, DEM_HALT);
+        }
         c_nnew = nnew;
         if (PRACT || EVAL) a.hout_cnt[q] = min(nnew, maxc);
         // gravity, once per particle
@@ -276,7 +285,7 @@ constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __restrict__ cnt, uint32_t m,
                                                               uint32_t ntiles, uint32_t* __restrict__ part,
                                                               const CtrlDev* ctrl) {
-    if (!ctrl->rebuild) return;
+    if (ctrl->rebuild != 1) return;   // no sort this step (or a void step)
     __shared__ uint32_t ws[SCAN_THREADS / 32];
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const uint32_t base = tile * SCAN_TILE;
@@ -299,7 +308,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* __
 
 // exclusive scan of part[0..nb) in one block of 1024 threads
 __global__ void __launch_bounds__(1024) k_scan_spine(uint32_t* part, uint32_t nb, const CtrlDev* ctrl) {
-    if (!ctrl->rebuild) return;
+    if (ctrl->rebuild != 1) return;   // no sort this step (or a void step)
     __shared__ uint32_t sh[1024];
     const uint32_t per = (nb + 1023) / 1024;
     const uint32_t b0 = threadIdx.x * per;
@@ -327,7 +336,7 @@ __global__ void __launch_bounds__(1024) k_scan_spine(uint32_t* part, uint32_t nb
 __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(uint32_t* __restrict__ cnt, uint32_t m, uint32_t ntiles,
                                                             const uint32_t* __restrict__ part, uint32_t* __restrict__ cs,
                                                             const CtrlDev* ctrl) {
-    if (!ctrl->rebuild) return;
+    if (ctrl->rebuild != 1) return;   // no sort this step (or a void step)
     __shared__ uint32_t ws[SCAN_THREADS / 32];
     const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -371,7 +380,7 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(uint32_t* __restrict
 
 __global__ void k_scatter(uint32_t n, const uint32_t* __restrict__ key, const uint32_t* __restrict__ rank,
                           const uint32_t* __restrict__ cs, uint32_t* __restrict__ tmp, const CtrlDev* ctrl) {
-    if (!ctrl->rebuild) return;
+    if (ctrl->rebuild != 1) return;   // no sort this step (or a void step)
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
         tmp[cs[key[q]] + rank[q]] = q;
 }
@@ -403,7 +412,7 @@ __global__ void k_reorder(uint32_t n, typename PR::State S0, typename PR::State 
                           const uint32_t* __restrict__ key, const uint32_t* __restrict__ cs,
                           const uint32_t* __restrict__ tmp, uint32_t* __restrict__ perm, uint32_t* __restrict__ skey,
                           float4* __restrict__ ref) {
-    if (!ctrl->rebuild) return;
+    if (ctrl->rebuild != 1) return;   // no sort this step (or a void step)
     const int cur = ctrl->cur;
     const typename PR::State A = cur ? S1 : S0;
     const typename PR::State B = cur ? S0 : S1;
@@ -423,7 +432,7 @@ __global__ void k_rank_cell(uint32_t n, typename PR::State S0, typename PR::Stat
                             const uint32_t* __restrict__ key, const uint32_t* __restrict__ cs,
                             const uint32_t* __restrict__ tmp, const uint32_t* __restrict__ hcnt_last,
                             uint32_t* __restrict__ canon, uint32_t* __restrict__ wkey) {
-    if (!ctrl->rebuild) return;
+    if (ctrl->rebuild != 1) return;   // no sort this step (or a void step)
     const typename PR::State B = ctrl->cur ? S0 : S1;
     for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
         const uint32_t p = tmp[s];
@@ -442,7 +451,7 @@ __global__ void k_rank_cell(uint32_t n, typename PR::State S0, typename PR::Stat
 // (cell, id) order), so every particle stays inside its scene's range of positions.
 __global__ void __launch_bounds__(256) k_window(uint32_t n, const SceneDev* scenes, int nscenes, const CtrlDev* ctrl,
                                                 const uint32_t* __restrict__ wkey, uint32_t* __restrict__ fin) {
-    if (!ctrl->rebuild) return;
+    if (ctrl->rebuild != 1) return;   // no sort this step (or a void step)
     __shared__ uint32_t s_key[256];
     __shared__ int32_t s_sc[256];
     const uint32_t w = blockDim.x;
@@ -468,7 +477,7 @@ __global__ void k_gather(uint32_t n, typename PR::State S0, typename PR::State S
                          const uint32_t* __restrict__ key, const uint32_t* __restrict__ canon,
                          const uint32_t* __restrict__ fin, uint32_t* __restrict__ perm, uint32_t* __restrict__ skey,
                          float4* __restrict__ ref) {
-    if (!ctrl->rebuild) return;
+    if (ctrl->rebuild != 1) return;   // no sort this step (or a void step)
     const typename PR::State A = ctrl->cur ? S1 : S0;
     const typename PR::State B = ctrl->cur ? S0 : S1;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
@@ -484,6 +493,8 @@ __global__ void k_gather(uint32_t n, typename PR::State S0, typename PR::State S
 // Step bookkeeping (one thread): after a sort the current set stays and springs are read
 // through the permutation next step; otherwise the next set becomes current.
 __global__ void k_end_step(CtrlDev* ctrl, StatusDev* st, int walk_mode) {
+    if (ctrl->rebuild & DEM_HALT) return;   // a void step changes nothing
+    ctrl->steps_done += 1;
     if (ctrl->rebuild) {
         ctrl->perm_valid = 1;
         ctrl->since = 0;
@@ -540,7 +551,7 @@ template <class PR>
 __global__ void k_hash(uint32_t n, const SceneDev* scenes, int nscenes, typename PR::State S0, typename PR::State S1,
                        const CtrlDev* ctrl, uint32_t* __restrict__ key, uint32_t* __restrict__ rank,
                        uint32_t* __restrict__ cnt, StatusDev* st) {
-    if (!ctrl->rebuild) return;
+    if (ctrl->rebuild != 1) return;   // no sort this step (or a void step)
     const typename PR::State B = ctrl->cur ? S0 : S1;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         const SceneDev& S = scenes[scene_of(scenes, nscenes, q)];
@@ -822,7 +833,7 @@ cudaError_t run_rebuild(Domain& d) {
 // Sets the condition of the step graph's sort node from the device-side decision, and
 // counts the sorts that run that way (one thread).
 __global__ void k_sort_cond(cudaGraphConditionalHandle h, CtrlDev* ctrl) {
-    const unsigned int go = ctrl->rebuild ? 1u : 0u;
+    const unsigned int go = ctrl->rebuild == 1 ? 1u : 0u;
     ctrl->cond_sorts += go;
     cudaGraphSetConditional(h, go);
 }
@@ -868,6 +879,7 @@ static cudaError_t force_impl(Domain& d, const typename PR::State& S0, const typ
     a.st = d.st;
     a.dbgF = dbgF;
     a.dbgT = dbgT;
+    a.halt = d.regrow;
     const uint32_t b = (uint32_t)d.block;
     const size_t smem = 2 * (size_t)d.maxc * b * sizeof(uint32_t);
     const uint32_t g = nblk(d.n, b);

@@ -55,6 +55,7 @@ struct ListArgs {
     StatusDev* st;
     double* dbgF;
     double* dbgT;
+    int halt;                    // 1: a capacity overflow makes the step void (DEM_HALT)
 };
 
 // ------------------------------------------------------------------- force pass
@@ -68,6 +69,8 @@ __global__ void __launch_bounds__(256, DEM_LIST_MIN_BLOCKS) k_list(ListArgs<PR> 
     constexpr bool TERMS = MODEL == 2;
     const unsigned full = 0xffffffffu;
     extern __shared__ uint32_t smem[];
+    // a void step (an earlier launch overflowed): nothing to do; one decision per warp
+    if (!EVAL && __any_sync(full, (a.ctrl->rebuild & DEM_HALT) != 0)) return;
     const int cur = a.ctrl->cur;
     const typename PR::State A = cur ? a.S1 : a.S0;
     const typename PR::State B = cur ? a.S0 : a.S1;
@@ -208,7 +211,10 @@ __global__ void __launch_bounds__(256, DEM_LIST_MIN_BLOCKS) k_list(ListArgs<PR> 
             ++c_wc;
             c_maxov = fmaxf(c_maxov, (float)delta);
         }
-        if (nnew > maxc) raise_status(a.st, ST_CAPACITY, (int32_t)q);
+        if (nnew > maxc) {
+            raise_status(a.st, ST_CAPACITY, (int32_t)q);
+            if (!EVAL && a.halt) atomicOr(&a.ctrl->rebuild, DEM_HALT);
+        }
         c_nnew = nnew;
         if (PRACT || EVAL) a.hout_cnt[q] = min(nnew, maxc);
         // gravity, once per particle
@@ -293,6 +299,7 @@ static cudaError_t force_list_impl(Domain& d, const typename PR::State& S0, cons
     a.st = d.st;
     a.dbgF = dbgF;
     a.dbgT = dbgT;
+    a.halt = d.regrow;
     const uint32_t b = (uint32_t)d.block;
     const size_t smem = (size_t)d.maxc * b * sizeof(uint32_t);
     const int model = d.model != 0 ? 1 : (d.terms != 0 ? 2 : 0);

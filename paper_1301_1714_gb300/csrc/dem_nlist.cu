@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256) k_nlist(uint32_t n, const SceneDev* scene
                                                const uint32_t* __restrict__ fin, uint32_t* __restrict__ ncnt,
                                                uint32_t* __restrict__ nl, size_t cap, uint32_t* __restrict__ wmask,
                                                StatusDev* st) {
-    if (!ctrl->rebuild) return;
+    if (ctrl->rebuild != 1) return;   // no sort this step (or a void step)
     const typename PR::State A = ctrl->cur ? S1 : S0;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x) {
         const SceneDev& S = scenes[scene_of(scenes, nscenes, q)];

@@ -406,20 +406,76 @@ def test_max_contacts_seen_counts_pairs_and_walls(list_mode):
     assert seen == cnt.max() and seen > 3
 
 
-def test_capacity_overflow_is_reported():
+@pytest.mark.parametrize("resort", [1, 0])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_contact_slot_overflow_grows_the_slots_and_reruns(resort, precision):
+    """A step in which a particle has more contacts than its slots is voided on the
+    device; dem_step doubles the slots (1 -> 2 -> 4 -> 8 here, one void step each) and
+    runs it again, so every bit of the state and of the springs equals a run that had
+    enough slots from the start. Walk mode and list mode."""
+    sc = scenes.box_lattice(seed=1, precision=precision)
+    x = compressed(sc, 0.95)          # six face neighbours in contact, plus walls
+    p = sc.params if resort == 1 else listed(sc.params)
+
+    def run(maxc):
+        h = dem.dem_create(dem.config_from_params(p, max_contacts=maxc))
+        try:
+            dem.dem_set_walls(h, p.walls)
+            dem.dem_set_particles(h, x, sc.v, sc.w, sc.r)
+            b0 = dem.dem_device_bytes(h)
+            dem.dem_step(h, 30)
+            st = dem.dem_get_state(h, sc.n)
+            d = dem.dem_get_diagnostics(h)
+            return st, dem.dem_get_history(h), dem.dem_device_bytes(h) - b0, d[13], dem.dem_max_contacts_seen(h)
+        finally:
+            dem.dem_destroy(h)
+
+    small, big = run(1), run(32)
+    for a, b in zip(small[0], big[0]):
+        assert np.array_equal(a, b)
+    assert np.array_equal(small[1], big[1])
+    assert small[2] > 0 and big[2] == 0      # the slots grew; 32 was enough
+    assert small[3] == big[3] == 30          # steps taken
+    assert 4 < small[4] <= 8
+
+
+def test_contact_overflow_past_64_keeps_the_state_before_the_step():
+    """A sphere of five radii with 80 small spheres pressed onto it: more contacts than
+    the largest capacity (64). dem_step grows the slots to 64, still overflows, and
+    reports DEM_ERR_CAPACITY with the state that the step started from; the handle stays
+    usable."""
+    rs, rb, m = 1e-3, 5e-3, 80
+    k = np.arange(m) + 0.5
+    th = np.arccos(1.0 - 2.0 * k / m)
+    ph = np.pi * (1.0 + 5.0 ** 0.5) * k
+    u = np.stack([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)], axis=1)
+    c = np.array([0.032, 0.032, 0.032])
+    x = np.vstack([c, c + u * (rb + rs - 1e-6)])
+    n = len(x)
+    v = np.zeros((n, 3)); w = np.zeros((n, 3))
+    r = np.full(n, rs, dtype=np.float32); r[0] = rb
     sc = scenes.box_lattice(seed=1)
-    x = compressed(sc, 0.95)
-    h = dem.dem_create(dem.config_from_params(sc.params, max_contacts=1))
+    p = sc.params.copy(g=(0.0, 0.0, 0.0), cell_size=2.0 * rb * (1.0 + 2.0 ** -9), walls=[])
+    h = dem.dem_create(dem.config_from_params(p, max_contacts=32))
     try:
-        dem.dem_set_walls(h, sc.params.walls)
-        dem.dem_set_particles(h, x, sc.v, sc.w, sc.r)
+        dem.dem_set_particles(h, x, v, w, r)
+        b0 = dem.dem_device_bytes(h)
         with pytest.raises(dem.DemError) as e:
-            dem.dem_step(h, 1)
-        assert e.value.status == 4
-        # the handle stays usable
-        dem.dem_get_state(h, sc.n)
+            dem.dem_step(h, 5)
+        assert e.value.status == dem.DEM_ERR_CAPACITY and "64" in str(e.value)
+        xs, vs, ws = dem.dem_get_state(h, n)
+        assert np.array_equal(xs, x) and np.array_equal(vs, v) and np.array_equal(ws, w)
+        assert dem.dem_device_bytes(h) > b0
+        assert dem.dem_get_diagnostics(h)[13] == 0
+        # usable afterwards: the small spheres alone, moving, run like the oracle
+        v2 = np.random.default_rng(3).normal(0.0, 0.5, size=(n - 1, 3))
+        dem.dem_set_particles(h, x[1:], v2, w[1:], r[1:])
+        dem.dem_step(h, 10)
+        x10, _, _ = dem.dem_get_state(h, n - 1)
     finally:
         dem.dem_destroy(h)
+    ref = oracle.State(p, x[1:], v2, w[1:], r[1:]).run(10)
+    assert np.max(np.abs(x10 - ref.x)) <= 1e-12
 
 
 def test_invalid_inputs_are_rejected():
