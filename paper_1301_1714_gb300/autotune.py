@@ -36,8 +36,11 @@ def apply(params, rmax: float, choice: Choice):
     return params.copy(resort_interval=choice.resort, skin=skin, cell_size=auto_cell_size(rmax, skin))
 
 
-def tune(params, x, v, w, r, candidates: Sequence[Tuple[int, int, float]] = DEFAULT_CANDIDATES, steps: int = 60,
-         warmup: int = 20, device: int = 0, cuda_stream=None, max_contacts: int = 0) -> Tuple[Choice, List[Choice]]:
+def tune(params, x, v, w, r, candidates: Sequence[Tuple[int, int, float]] = DEFAULT_CANDIDATES, steps: int = 150,
+         warmup: int = 50, device: int = 0, cuda_stream=None, max_contacts: int = 0) -> Tuple[Choice, List[Choice]]:
+    """Times each candidate for `steps` steps after `warmup` (long enough that a list-mode
+    candidate has sorted once with known contact counts, which order its windows, and that
+    the timed steps hold several sorts); returns the fastest and the table."""
     rmax = float(max(r)) if len(r) else 1.0
     table: List[Choice] = []
     for block, resort, sk in candidates:
