@@ -86,10 +86,10 @@ enum { DEM_TERM_NO_ATTRACTION = 1, DEM_TERM_ROLLING = 2, DEM_TERM_ETA_T = 4, DEM
  *              steps. 0 and K > 1 need skin > 0; they find exactly the same contacts.
  *              In these modes the library numbers grid cells in cubic bricks internally
  *              (the largest edge of 2, 4, 8 or 16 cells that pads the grid by at most 1/8;
- *              row-major cells when none does) and stores each window of block_size
- *              consecutive (cell, id) positions ordered by the particles' last contact
- *              counts, so the force kernel's warps get similar amounts of work; a list
- *              holds at most 64
+ *              row-major cells when none does) and stores each window of four blocks
+ *              of consecutive (cell, id) positions (at most 1,024) ordered by the
+ *              particles' last contact counts, so the force kernel's warps get similar
+ *              amounts of work; a list holds at most 64
  *              candidates in ascending partner id (a fuller one makes dem_step return
  *              DEM_ERR_CAPACITY), so a particle's contacts are summed in that order and
  *              results do not depend on when the sorts happened.

@@ -428,9 +428,9 @@ __global__ void k_reorder(uint32_t n, typename PR::State S0, typename PR::State 
         reorder_one<PR>(s, A, B, key, cs, tmp, perm, skey, ref);
 }
 
-// List mode stores the sorted particles in (cell, id) order within windows of the force
-// pass's block size, each window ordered by the particles' contact counts in the step
-// just finished (descending; ties keep the (cell, id) order). The lanes of a warp run
+// List mode stores the sorted particles in (cell, id) order within windows of
+// DEM_WINDOW_MULT force blocks, each window ordered by the particles' contact counts in
+// the step just finished (descending; ties keep the (cell, id) order). The lanes of a warp run
 // their candidate lists in lockstep, so grouping similar counts shortens the longest
 // lane's loop; a particle's own sums keep their order, so results do not change.
 // Three passes replace k_reorder: the (cell, id) position of every particle, its final
