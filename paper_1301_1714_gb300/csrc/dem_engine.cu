@@ -964,9 +964,12 @@ dem_status dem_run_until(dem_handle* h, int64_t max_steps, double disp_threshold
     int ok = 0;
     while (done < max_steps) {
         const int64_t k = std::min(check_every, max_steps - done);
+        const int64_t s0 = h->steps;
         const dem_status st = dem_step(h, k);
         if (st != DEM_OK) {
-            if (steps_done) *steps_done = done + k;
+            // the steps dem_step took (fewer than k when a step was voided by a capacity
+            // overflow it could not grow past)
+            if (steps_done) *steps_done = done + (h->steps - s0);
             return st;
         }
         done += k;
